@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused LCT (XFT) kernel.
+
+Workload (default): 16384 complex64 signals of N = 4096 samples, per-signal
+parameters from generator G1 (a, d ~ U[-2, 2], |b| ~ U[0.2, 2] with random
+sign, c = (ad - 1)/b; Gaussian-windowed random chirps plus 1e-3 noise), one
+batch plan.  One step = one lct_execute over the whole batch (the whole hot
+path: chirp, 4096-point DFT, chirp + scale, in one kernel).  Inputs are
+resident in HBM; each buffer (512 MiB) is larger than L2.
+
+Reported next to it: the plain FP64 GPU path (chirp kernel, cuFFT Z2Z,
+chirp kernel) on the same batch, an end-to-end number with host buffers,
+and the CPU oracle (O(N^2) FP64) on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "LCT points/s at N=4096 batched vs plain FP64 GPU path at <=1e-5 rel err; %HBM"
+N_DEFAULT, COUNT_DEFAULT = 4096, 16384
+BYTES_PER_POINT = 16          # complex64: 8 B read + 8 B written
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/xft_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_xft_fused_f32_n4096.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--count", type=int, default=COUNT_DEFAULT)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_launch(n_points: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None), scaled to this launch size."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            j = json.load(fh)
+    except Exception:
+        return None
+    if j.get("kernel_hash") != kernel_hash():
+        return None
+    per_point = float(j["dram_bytes"]) / float(j["points"])
+    return per_point * n_points
+
+
+# ---------------------------------------------------------------------------
+# clocks: nvidia-smi sampled in the background
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.t is not None:
+                self.t.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        sm, smax, reasons = [], [], set()
+        for ts, line in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(x, params, f, min_seconds: float = 10.0, max_signals: int = 1024):
+    import oracle as O
+    O.build()
+    done, t0 = 0, time.perf_counter()
+    chunk = 8
+    while done < max_signals:
+        s = slice(done, done + chunk)
+        O.lct(f[s].astype(np.complex128), params[s])
+        done += f[s].shape[0]
+        if time.perf_counter() - t0 >= min_seconds or done >= f.shape[0]:
+            break
+    dt = time.perf_counter() - t0
+    N = f.shape[1]
+    return done * N / dt, done, dt, O.num_threads()
+
+
+def reference_arm(args, rank, world):
+    """The CPU oracle as the reference implementation (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle as O
+    N = args.n
+    O.build()
+    x = O.nodes(N)
+    per_step = 2
+    count = per_step * (args.steps + args.warmup)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096, dtype=np.complex64)
+    f64 = f.astype(np.complex128)
+    for s in range(args.warmup):
+        sl = slice(s * per_step, (s + 1) * per_step)
+        O.lct(f64[sl], params[sl])
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        sl = slice(s * per_step, (s + 1) * per_step)
+        O.lct(f64[sl], params[sl])
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step * N / dt
+    sample = "%d signals of N=%d per step from the G1 workload (seed %d)" % (per_step, N, W.SEED_UNIFORM_4096)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "uniform batch N=4096 complex64, G1 per-signal parameters (bounded sample)",
+                   "N": N},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": O.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_0912_1379_gb300 as lct
+
+    lct.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    N, count = args.n, args.count
+    x = lct.lct_input_grid(N)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)
+    plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+    h_in = torch.from_numpy(f).pin_memory()
+    d_in = h_in.cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    n_points = count * N
+
+    def step():
+        plan.execute(d_in, d_out, count, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = lct.lct_device_status(plan.handle)
+    if status != 0:
+        raise RuntimeError("device status %d after warm-up" % status)
+
+    sampler = ClockSampler(local)
+    if not args.no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier()
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+    ms_per_step = ms_total / args.steps
+    # Clock samples need ~1 s under load; if the K steps were shorter, the same
+    # launch loop continues for 1.5 s and the samples come from both.
+    clock_note = "timed region"
+    if t_wall1 - t_wall0 < 1.0 and not args.no_clocks:
+        t_end = time.time() + 1.5
+        while time.time() < t_end:
+            for _ in range(50):
+                step()
+            torch.cuda.synchronize()
+        t_wall1 = time.time()
+        clock_note = "timed region + 1.5 s continuation of the same launch loop"
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+    if clocks is not None:
+        clocks["window"] = clock_note
+
+    value = world * n_points / (ms_per_step * 1e-3)
+    peak, peak_kind = measured_peak()
+    achieved = n_points * BYTES_PER_POINT / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_per_launch(n_points),
+                "kernel": "k_xft_fused<12, float> (N=4096, complex64)",
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}
+
+    # plain FP64 path on the same batch
+    plain = None
+    if not args.no_plain:
+        plan.set_precision(lct.LCT_PREC_PLAIN64)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        plain = {"value": world * n_points / (pms * 1e-3), "unit": "points/s", "ms_per_step": pms,
+                 "path": "chirp kernel + cuFFT Z2Z + chirp kernel, FP64 workspace"}
+        plan.set_precision(lct.LCT_PREC_NATIVE)
+        torch.cuda.synchronize()
+        # release the plain path's workspace
+        plan.destroy()
+        plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+        step()
+        torch.cuda.synchronize()
+
+    # end to end with host buffers: H2D copy, transform, D2H copy per step
+    e2e = None
+    if not args.no_e2e:
+        h_out = torch.empty_like(h_in).pin_memory()
+
+        def e2e_step():
+            d_in.copy_(h_in, non_blocking=True)
+            plan.execute(d_in, d_out, count, stream)
+            h_out.copy_(d_out, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        nbytes = count * N * 8
+        e2e = {"value": world * n_points / (ems * 1e-3), "unit": "points/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ems,
+               "api": "lct_execute on device buffers with pinned-host copies on the same stream"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, nsig, dt, cores = cpu_oracle_rate(x, params, f)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d signals of the %d x N=%d workload, %.1f s" % (nsig, count, N, dt)}
+
+    plan.destroy()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "uniform batch %d x N=%d complex64, G1 per-signal (a,b,c,d), seed %d"
+                                   % (count, N, W.SEED_UNIFORM_4096),
+                       "signals_per_gpu": count, "N": N, "transforms_per_s": value / N,
+                       "l2": "inputs larger than L2 (512 MiB per buffer), no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "plain64": plain,
+            "speedup_vs_plain64": (plain["ms_per_step"] / ms_per_step) if plain else None,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

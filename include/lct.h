@@ -1,0 +1,153 @@
+/*
+ * lct.h -- C ABI of the GB300 library for the discrete linear canonical
+ * transform (LCT) of Campos & Figueroa, "A fast algorithm for the linear
+ * canonical transform" (the XFT).
+ *
+ * The transform (Sec. 3, eq. (lctdos), the matrix L = S1 F S2 and the
+ * Algorithm).  For N = 2^p samples f_k of a function at the asymptotic
+ * Hermite nodes of eq. (asymcer),
+ *     x_k = (2k - N + 1) pi / (2 sqrt(2N)),   k = 0..N-1   (0-based),
+ * with spacing dx = pi / sqrt(2N) (eq. (deltk)), the library returns, for
+ * parameters (a, b, c, d) with ad - bc = 1 and b != 0,
+ *     G_j = dx / sqrt(2 pi i b) * e^{i d y_j^2 / (2b)}
+ *           * sum_k e^{-i x_k y_j / b} e^{i a x_k^2 / (2b)} f_k,
+ *     y_j = 4 b x_j / pi,
+ * computed in O(N log N) as chirp - DFT - chirp (the Algorithm of Sec. 3,
+ * with the DFT taken with the forward sign e^{-2 pi i jk/N} and conjugated
+ * centring phases, the reading under which it reproduces eq. (lctdos)).
+ * For b == 0 (definition below eq. (lctuno)) it returns
+ *     G_j = sqrt(d) e^{i c d y_j^2 / 2} f_j  on the output points y_j = x_j / d.
+ * sqrt is the principal root.  For complex parameters (the fractional
+ * transform with complex z, Sec. 1) the returned values are
+ * Ghat_j = G_j e^{-rho_j}, rho_j = -Im(d y_j^2 / (2b)) (b != 0) or
+ * -Im(c d y_j^2 / 2) (b == 0), which removes the real exponential of the
+ * output chirp; lct_output_grid returns rho.  For real parameters rho = 0.
+ *
+ * Data layout.  Signals are complex, interleaved (re, im), row-major
+ * [batch][N]: LCT_C64 = 2 x float (8 bytes per sample), LCT_C128 = 2 x
+ * double (16 bytes).  Device pointers must be aligned to the sample size.
+ *
+ * Ownership.  The caller owns every buffer passed in.  A plan owns its
+ * parameter descriptors, tables and workspace on the device, created on the
+ * first execute on the current device and freed by lct_plan_destroy.
+ *
+ * Errors.  Every entry returns an lct_status; nothing traps.  Execution is
+ * asynchronous on the given stream and performs no host synchronisation
+ * (except lct_device_status, which synchronises).  Device-side per-item
+ * errors are recorded in a status word read by lct_device_status.
+ *
+ * Streams are CUDA runtime streams (cudaStream_t); NULL is the legacy
+ * default stream.
+ */
+#ifndef LCT_H
+#define LCT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* lct_stream_t;   /* == cudaStream_t */
+
+typedef struct lct_plan_s* lct_plan;        /* opaque, owned by the library */
+
+typedef enum { LCT_C64 = 0, LCT_C128 = 1 } lct_dtype;
+
+/* Arithmetic of the transform.
+ *  NATIVE      fused chirp-DFT-chirp kernel in the sample precision
+ *              (FP32 for LCT_C64, FP64 for LCT_C128); phases exact (below).
+ *  PLAIN64     unfused FP64 baseline: a chirp kernel, a library FFT (cuFFT
+ *              Z2Z, forward sign) on an FP64 workspace, a chirp+scale kernel.
+ *  SPLIT_BF16, SPLIT_FP16, FP16
+ *              reserved for the tensor-core DFT; LCT_ERR_UNSUPPORTED until built.
+ * Phases: every chirp phase is a turn fraction held as a fixed-point integer
+ * (64 bits of fraction for FP32 paths, 128 for FP64 paths) and multiplied by
+ * the integer m^2 (m = 2k - N + 1) with wrap-around, so no phase loses
+ * accuracy as N or a/b grows. */
+typedef enum {
+    LCT_PREC_NATIVE = 0,
+    LCT_PREC_SPLIT_BF16 = 1,
+    LCT_PREC_SPLIT_FP16 = 2,
+    LCT_PREC_FP16 = 3,
+    LCT_PREC_PLAIN64 = 4
+} lct_precision;
+
+typedef enum {
+    LCT_OK = 0,
+    LCT_ERR_ARG = 1,             /* null pointer, bad count/batch, bad z */
+    LCT_ERR_N = 2,               /* N not a power of two in [2, 65536] */
+    LCT_ERR_NOT_SYMPLECTIC = 3,  /* |ad - bc - 1| > 1e-9 max(1, |ad|, |bc|) */
+    LCT_ERR_DTYPE = 4,
+    LCT_ERR_ALIGN = 5,           /* pointer not aligned to the sample size */
+    LCT_ERR_OOM = 6,
+    LCT_ERR_CUDA = 7,            /* a CUDA runtime or cuFFT call failed */
+    LCT_ERR_DEVICE = 8,          /* a kernel recorded a per-item error */
+    LCT_ERR_TIMEOUT = 9,         /* a bounded device wait gave up */
+    LCT_ERR_UNSUPPORTED = 10     /* combination not implemented */
+} lct_status;
+
+/* Plan for N-point transforms with real parameters (a, b, c, d), ad - bc = 1
+ * (Sec. 1).  c is used only when b == 0.  Host-only: touches no GPU. */
+lct_status lct_plan_create(lct_plan* out, int64_t N, double a, double b, double c, double d,
+                           lct_dtype dtype);
+
+/* Same with complex parameters: abcd_reim = {a_re, a_im, b_re, b_im, c_re,
+ * c_im, d_re, d_im} (the fractional transform for complex z, Sec. 1). */
+lct_status lct_plan_create_complex(lct_plan* out, int64_t N, const double abcd_reim[8],
+                                   lct_dtype dtype);
+
+/* Batch plan: `count` independent signals, signal s of length N[s] (power of
+ * two) with parameters abcd_reim[8 s .. 8 s + 7] (layout as above), stored at
+ * element offset offsets[s] of the in/out buffers.  All arrays are host
+ * memory, copied by the plan.  Host-only. */
+lct_status lct_plan_create_batch(lct_plan* out, int64_t count, const int64_t* N,
+                                 const double* abcd_reim, const int64_t* offsets,
+                                 lct_dtype dtype);
+
+lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
+
+/* Apply the plan.  in/out: device buffers in the plan's dtype.  For a plan
+ * from lct_plan_create[_complex], `batch` signals of N samples, row-major.
+ * For a batch plan, `batch` must equal its count.  in == out is allowed.
+ * batch == 0 is a no-op.  Asynchronous on `stream`. */
+lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
+                       lct_stream_t stream);
+
+/* Discrete fractional Fourier transform F_z with the normalisation of
+ * eq. (eqifft): F_z = sqrt(2/(1 - z^2)) sqrt(2 pi i b) LCT(a, b, c, d) with
+ * a = d = (z + 1/z)/2, b = (1/z - z)/(2i), c = i (1/z - z)/2, for
+ * 0 < |z| <= 1 (|z| = 1, z != +-1: real-angle transform; z = +-1:
+ * sqrt(2 pi) f on y_j = x_j / z).  Output points y_j = 4 b(z) x_j / pi;
+ * the values are returned as G e^{-rho} (see above).  in/out as lct_execute. */
+lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
+                        int64_t batch, lct_dtype dtype, lct_stream_t stream);
+
+/* Output points and rho of signal `index` of the plan (0 for single plans):
+ * y_reim receives N complex points (2N doubles), rho N doubles (may be
+ * NULL).  Host-only. */
+lct_status lct_output_grid(lct_plan plan, int64_t index, double* y_reim, double* rho);
+
+/* Input nodes x_k of eq. (asymcer), N doubles.  Host-only. */
+lct_status lct_input_grid(int64_t N, double* x);
+
+/* Fixed-point phase constants of signal `index` (for inspection and tests):
+ * out[0..1] = Re(beta_in)/(2 pi) as a 128-bit turn fraction (hi, lo words),
+ * out[2..3] = Re(beta_out)/(2 pi) likewise, out[4] = constant output turn
+ * offset (64-bit fraction), where the pre-chirp is e^{i beta_in m^2} and the
+ * post-chirp e^{i beta_out m^2}, m = 2k - N + 1.  Host-only. */
+lct_status lct_plan_phase_turns(lct_plan plan, int64_t index, uint64_t out[5]);
+
+/* Synchronise `stream`, read and clear the plan's device status word. */
+lct_status lct_device_status(lct_plan plan, lct_stream_t stream);
+
+lct_status lct_plan_destroy(lct_plan plan);
+
+const char* lct_status_string(lct_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCT_H */

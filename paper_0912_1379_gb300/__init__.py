@@ -1,0 +1,250 @@
+"""Python binding of the GB300 discrete LCT library (include/lct.h).
+
+Argument marshalling only: every function forwards to the native entry point
+of the same name in liblct.so (built in-tree by ``_build.build()``); every
+step of the transform runs in the library's CUDA kernels.  PyTorch is used
+only for device memory and streams.  If liblct.so is missing the import of
+any entry point raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+LCT_C64, LCT_C128 = 0, 1
+LCT_PREC_NATIVE, LCT_PREC_SPLIT_BF16, LCT_PREC_SPLIT_FP16, LCT_PREC_FP16, LCT_PREC_PLAIN64 = range(5)
+STATUS = ["LCT_OK", "LCT_ERR_ARG", "LCT_ERR_N", "LCT_ERR_NOT_SYMPLECTIC", "LCT_ERR_DTYPE",
+          "LCT_ERR_ALIGN", "LCT_ERR_OOM", "LCT_ERR_CUDA", "LCT_ERR_DEVICE", "LCT_ERR_TIMEOUT",
+          "LCT_ERR_UNSUPPORTED"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LctError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__("%s: %s (%s)" % (where, name, _status_string(status)))
+
+
+def build(force: bool = False) -> str:
+    """Compile liblct.so for sm_103a (in-tree)."""
+    return _build.build(force=force)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("liblct.so is not built (call paper_0912_1379_gb300.build()); "
+                               "there is no fallback path")
+        lib = ctypes.CDLL(_build.LIB)
+        i64, f64, vp, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_int64)
+        up = ctypes.POINTER(ctypes.c_uint64)
+        plan_p = ctypes.POINTER(vp)
+        sig = {
+            "lct_plan_create": [plan_p, i64, f64, f64, f64, f64, i32],
+            "lct_plan_create_complex": [plan_p, i64, dp, i32],
+            "lct_plan_create_batch": [plan_p, i64, lp, dp, lp, i32],
+            "lct_plan_set_precision": [vp, i32],
+            "lct_execute": [vp, vp, vp, i64, vp],
+            "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
+            "lct_output_grid": [vp, i64, dp, dp],
+            "lct_input_grid": [i64, dp],
+            "lct_plan_phase_turns": [vp, i64, up],
+            "lct_device_status": [vp, vp],
+            "lct_plan_destroy": [vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = i32
+        lib.lct_status_string.argtypes = [i32]
+        lib.lct_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _status_string(status: int) -> str:
+    try:
+        return _load().lct_status_string(status).decode()
+    except Exception:  # library not loadable while formatting an error
+        return "?"
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise LctError(status, where)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def dtype_code(torch_dtype) -> int:
+    import torch
+    if torch_dtype == torch.complex64:
+        return LCT_C64
+    if torch_dtype == torch.complex128:
+        return LCT_C128
+    raise TypeError("samples must be complex64 or complex128, got %s" % (torch_dtype,))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as include/lct.h)
+# ---------------------------------------------------------------------------
+def lct_plan_create(N: int, a: float, b: float, c: float, d: float, dtype: int = LCT_C64) -> int:
+    h = ctypes.c_void_p()
+    _check(_load().lct_plan_create(ctypes.byref(h), N, a, b, c, d, dtype), "lct_plan_create")
+    return h.value
+
+
+def lct_plan_create_complex(N: int, abcd, dtype: int = LCT_C64) -> int:
+    p = np.ascontiguousarray(np.asarray(abcd, dtype=np.complex128).view(np.float64))
+    if p.shape != (8,):
+        raise ValueError("abcd must hold 4 complex values")
+    h = ctypes.c_void_p()
+    _check(_load().lct_plan_create_complex(ctypes.byref(h), N,
+                                           p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           dtype), "lct_plan_create_complex")
+    return h.value
+
+
+def lct_plan_create_batch(N, abcd, offsets, dtype: int = LCT_C64) -> int:
+    Ns = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
+    p = np.ascontiguousarray(np.asarray(abcd, dtype=np.complex128).reshape(len(Ns), 4)
+                             .view(np.float64).reshape(-1))
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.shape != Ns.shape:
+        raise ValueError("offsets must have one entry per signal")
+    h = ctypes.c_void_p()
+    lp = ctypes.POINTER(ctypes.c_int64)
+    _check(_load().lct_plan_create_batch(ctypes.byref(h), len(Ns), Ns.ctypes.data_as(lp),
+                                         p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         off.ctypes.data_as(lp), dtype), "lct_plan_create_batch")
+    return h.value
+
+
+def lct_plan_set_precision(plan: int, precision: int) -> None:
+    _check(_load().lct_plan_set_precision(plan, precision), "lct_plan_set_precision")
+
+
+def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
+    _check(_load().lct_execute(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
+           "lct_execute")
+
+
+def frft_execute(N: int, z: complex, inp, out, batch: int, dtype: int = LCT_C64, stream=None) -> None:
+    z = complex(z)
+    _check(_load().frft_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
+                                _stream_handle(stream)), "frft_execute")
+
+
+def lct_output_grid(plan: int, index: int = 0, N: Optional[int] = None):
+    """(y complex128 [N], rho float64 [N]) of signal `index`."""
+    if N is None:
+        raise ValueError("pass N (the signal length of that index)")
+    y = np.empty(2 * N, dtype=np.float64)
+    rho = np.empty(N, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_load().lct_output_grid(plan, index, y.ctypes.data_as(dp), rho.ctypes.data_as(dp)),
+           "lct_output_grid")
+    return y.view(np.complex128), rho
+
+
+def lct_input_grid(N: int) -> np.ndarray:
+    x = np.empty(N, dtype=np.float64)
+    _check(_load().lct_input_grid(N, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "lct_input_grid")
+    return x
+
+
+def lct_plan_phase_turns(plan: int, index: int = 0):
+    out = (ctypes.c_uint64 * 5)()
+    _check(_load().lct_plan_phase_turns(plan, index, out), "lct_plan_phase_turns")
+    return tuple(int(v) for v in out)
+
+
+def lct_device_status(plan: int, stream=None) -> int:
+    """Synchronise and return the device status (0 = ok); does not raise."""
+    return int(_load().lct_device_status(plan, _stream_handle(stream)))
+
+
+def lct_plan_destroy(plan: int) -> None:
+    _check(_load().lct_plan_destroy(plan), "lct_plan_destroy")
+
+
+def lct_status_string(status: int) -> str:
+    return _status_string(status)
+
+
+# ---------------------------------------------------------------------------
+# convenience: an owning plan object
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owning wrapper of an lct_plan handle."""
+
+    def __init__(self, handle: int, N, dtype: int):
+        self.handle = handle
+        self.N = N
+        self.dtype = dtype
+
+    @classmethod
+    def create(cls, N: int, a, b, c, d, dtype: int = LCT_C64) -> "Plan":
+        if any(isinstance(v, complex) for v in (a, b, c, d)):
+            return cls(lct_plan_create_complex(N, [a, b, c, d], dtype), N, dtype)
+        return cls(lct_plan_create(N, a, b, c, d, dtype), N, dtype)
+
+    @classmethod
+    def batch(cls, N, abcd, offsets, dtype: int = LCT_C64) -> "Plan":
+        return cls(lct_plan_create_batch(N, abcd, offsets, dtype), N, dtype)
+
+    def set_precision(self, precision: int) -> "Plan":
+        lct_plan_set_precision(self.handle, precision)
+        return self
+
+    def execute(self, inp, out, batch: int, stream=None) -> None:
+        lct_execute(self.handle, inp, out, batch, stream)
+
+    def destroy(self) -> None:
+        if self.handle:
+            lct_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

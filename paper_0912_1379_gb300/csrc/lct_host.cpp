@@ -1,0 +1,538 @@
+// Host side of the LCT library: parameter validation, exact phase constants,
+// plans, and dispatch to the kernels.  Implements include/lct.h.
+//
+// Phase constants.  The chirp coefficients (Sec. 3, Algorithm, steps 1-2)
+//   Re(beta_in)/(2 pi)  = Re(a/b) pi / (32 N)
+//   Re(beta_out)/(2 pi) = Re(b d) / (2 pi N)
+// are evaluated in double-double arithmetic (about 106 significant bits)
+// from the exact FP64 parameters and reduced modulo one turn into 128-bit
+// fixed-point fractions.  The output constant e^{-i pi (N-1)^2/(2N)} is an
+// exact dyadic turn fraction; the argument of dx/sqrt(2 pi i b) is added to
+// it in double precision.
+#include "lct_internal.h"
+#include "../../include/lct.h"
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// double-double arithmetic (Dekker / Knuth error-free transformations)
+// ---------------------------------------------------------------------------
+struct dd { double hi, lo; };
+
+dd two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+dd quick_two_sum(double a, double b) {
+    double s = a + b;
+    return {s, b - (s - a)};
+}
+dd two_prod(double a, double b) {
+    double p = a * b;
+    return {p, std::fma(a, b, -p)};
+}
+dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi);
+    dd t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+dd dd_mul(dd a, dd b) {
+    dd p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return quick_two_sum(p.hi, p.lo);
+}
+dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(b, {q1, 0.0}));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(b, {q2, 0.0}));
+    double q3 = r.hi / b.hi;
+    return dd_add(quick_two_sum(q1, q2), {q3, 0.0});
+}
+dd dd_ldexp(dd a, int e) { return {std::ldexp(a.hi, e), std::ldexp(a.lo, e)}; }
+
+// pi to about 107 bits
+const dd DD_PI = {3.141592653589793116e+00, 1.224646799147353207e-16};
+
+typedef unsigned __int128 u128;
+
+// round(v * 2^128) mod 2^128 for |v| < 1.
+u128 frac_to_q128(double v) {
+    if (v == 0.0) return 0;
+    int e;
+    double m = std::frexp(std::fabs(v), &e);          // |v| = m 2^e, m in [1/2, 1)
+    uint64_t M = (uint64_t)std::ldexp(m, 53);         // exact 53-bit integer
+    int sh = e - 53 + 128;                            // |v| 2^128 = M 2^sh, sh <= 75
+    u128 r;
+    if (sh >= 0) r = (u128)M << sh;
+    else if (sh > -64) r = (u128)((M + ((uint64_t)1 << (-sh - 1))) >> (-sh));
+    else r = 0;
+    return v < 0 ? (u128)0 - r : r;
+}
+
+// Fractional part of a double-double as a 128-bit turn fraction.
+void dd_to_turns128(dd t, uint64_t* hi, uint64_t* lo) {
+    // x - trunc(x) is exact for every double (x - floor(x) is not for small
+    // negative x); the signed fractions wrap modulo one turn below.
+    double fh = t.hi - std::trunc(t.hi);
+    double fl = t.lo - std::trunc(t.lo);
+    u128 q = frac_to_q128(fh) + frac_to_q128(fl);
+    *hi = (uint64_t)(q >> 64);
+    *lo = (uint64_t)q;
+}
+
+// Fractional part of a double (|v| moderate) as a 64-bit turn fraction.
+uint64_t double_to_turns64(double v) {
+    uint64_t hi, lo;
+    dd_to_turns128({v, 0.0}, &hi, &lo);
+    return hi + (lo >> 63);
+}
+
+typedef std::complex<double> cplx;
+
+int ilog2_exact(int64_t N) {
+    if (N < 2 || N > 65536) return -1;
+    if ((N & (N - 1)) != 0) return -1;
+    int p = 0;
+    while ((int64_t(1) << p) < N) ++p;
+    return p;
+}
+
+// Re(x/y) of complex FP64 numbers, in double-double.
+dd dd_re_div(cplx x, cplx y) {
+    dd num = dd_add(two_prod(x.real(), y.real()), two_prod(x.imag(), y.imag()));
+    dd den = dd_add(two_prod(y.real(), y.real()), two_prod(y.imag(), y.imag()));
+    return dd_div(num, den);
+}
+// Re(x*y) in double-double.
+dd dd_re_mul(cplx x, cplx y) {
+    return dd_sub(two_prod(x.real(), y.real()), two_prod(x.imag(), y.imag()));
+}
+
+bool symplectic(cplx a, cplx b, cplx c, cplx d) {
+    cplx ad = a * d, bc = b * c;
+    double tol = 1e-9 * std::fmax(1.0, std::fmax(std::abs(ad), std::abs(bc)));
+    return std::abs(ad - bc - 1.0) <= tol;
+}
+
+// Build the descriptor of one signal.  Returns LCT_OK or a validation error.
+lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
+    int log2n = ilog2_exact(N);
+    if (log2n < 0) return LCT_ERR_N;
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(p[i])) return LCT_ERR_ARG;
+    cplx a(p[0], p[1]), b(p[2], p[3]), c(p[4], p[5]), d(p[6], p[7]);
+    if (!symplectic(a, b, c, d)) return LCT_ERR_NOT_SYMPLECTIC;
+    std::memset(D, 0, sizeof(*D));
+    D->offset = offset;
+    D->log2n = log2n;
+    uint64_t hi, lo;
+    if (b == cplx(0.0, 0.0)) {
+        // b = 0: G_j = sqrt(d) e^{i c x_j^2 / (2d)} f_j on y_j = x_j / d;
+        // c x^2/(2d) = Re(c/d) pi^2 m^2/(16N) -> turns Re(c/d) pi / (32N).
+        D->kind = LCT_KIND_DIAG;
+        dd t = dd_ldexp(dd_mul(dd_re_div(c, d), DD_PI), -(5 + log2n));
+        dd_to_turns128(t, &hi, &lo);
+        D->out_hi = hi;
+        D->out_lo = lo;
+        cplx sd = std::sqrt(d);                       // principal root
+        D->scale = std::abs(sd);
+        D->out_c = double_to_turns64(std::arg(sd) / (2.0 * M_PI));
+        return LCT_OK;
+    }
+    D->kind = LCT_KIND_XFT;
+    // pre-chirp a x_k^2/(2b) = (a/b) pi^2 m^2 / (16 N): turns (a/b) pi / (32 N)
+    dd tin = dd_ldexp(dd_mul(dd_re_div(a, b), DD_PI), -(5 + log2n));
+    dd_to_turns128(tin, &hi, &lo);
+    D->in_hi = hi;
+    D->in_lo = lo;
+    cplx ab = a / b;
+    double decay = ab.imag() * M_PI * M_PI / (16.0 * (double)N);
+    D->decay = decay;
+    if (decay != 0.0) D->flags |= LCT_FLAG_DECAY;
+    // post-chirp d y_j^2/(2b) = b d m^2 / N: turns Re(b d) / (2 pi N)
+    dd tout = dd_ldexp(dd_div(dd_re_mul(b, d), DD_PI), -(1 + log2n));
+    dd_to_turns128(tout, &hi, &lo);
+    D->out_hi = hi;
+    D->out_lo = lo;
+    // constant: -(N-1)^2/(4N) turns (exact) + arg(dx / sqrt(2 pi i b)) / (2 pi)
+    uint64_t r = (uint64_t)(((N - 1) * (N - 1)) % (4 * N));
+    uint64_t centre = (uint64_t)0 - (r << (62 - log2n));       // -r / (4N) as Q0.64
+    double dx = M_PI / std::sqrt(2.0 * (double)N);
+    cplx pre = dx / std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
+    D->scale = std::abs(pre);
+    D->out_c = centre + double_to_turns64(std::arg(pre) / (2.0 * M_PI));
+    return LCT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct lct_plan_s {
+    lct_dtype dtype = LCT_C64;
+    lct_precision prec = LCT_PREC_NATIVE;
+    bool is_batch = false;
+    int64_t count = 1;
+    int64_t N0 = 0;                 // common N (uniform plans); 0 when ragged
+    std::vector<int64_t> N;
+    std::vector<double> abcd;       // count x 8
+    std::vector<lct_desc> desc;     // count descriptors
+    // device state
+    std::mutex mu;
+    int device = -1;
+    lct_desc* d_desc = nullptr;
+    int32_t* d_status = nullptr;
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+    cufftHandle fft = 0;
+    bool fft_valid = false;
+    int64_t fft_n = 0, fft_batch = 0;
+};
+
+namespace {
+
+void release_device(lct_plan p) {
+    if (p->device < 0) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    if (p->fft_valid) cufftDestroy(p->fft);
+    cudaFree(p->d_desc);
+    cudaFree(p->d_status);
+    cudaFree(p->d_work);
+    if (cur != p->device && cur >= 0) cudaSetDevice(cur);
+    p->fft_valid = false;
+    p->d_desc = nullptr;
+    p->d_status = nullptr;
+    p->d_work = nullptr;
+    p->work_bytes = 0;
+    p->device = -1;
+}
+
+// Upload descriptors to the current device (once per device).
+lct_status ensure_device(lct_plan p) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LCT_ERR_CUDA;
+    if (p->device == dev) return LCT_OK;
+    release_device(p);
+    size_t bytes = sizeof(lct_desc) * p->desc.size();
+    if (cudaMalloc(&p->d_desc, bytes) != cudaSuccess) return LCT_ERR_OOM;
+    if (cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(p->d_desc);
+        p->d_desc = nullptr;
+        return LCT_ERR_OOM;
+    }
+    if (cudaMemcpy(p->d_desc, p->desc.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(p->d_desc);
+        cudaFree(p->d_status);
+        p->d_desc = nullptr;
+        p->d_status = nullptr;
+        return LCT_ERR_CUDA;
+    }
+    p->device = dev;
+    return LCT_OK;
+}
+
+lct_status check_ptr(const void* ptr, lct_dtype dt) {
+    if (!ptr) return LCT_ERR_ARG;
+    uintptr_t align = dt == LCT_C64 ? 8 : 16;
+    if (((uintptr_t)ptr) % align) return LCT_ERR_ALIGN;
+    return LCT_OK;
+}
+
+lct_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return LCT_OK;
+    if (e == cudaErrorMemoryAllocation) return LCT_ERR_OOM;
+    return LCT_ERR_CUDA;
+}
+
+lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t* N,
+                    const double* abcd, const int64_t* offsets, bool is_batch) {
+    if (!out) return LCT_ERR_ARG;
+    *out = nullptr;
+    if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
+    if (count < 1) return LCT_ERR_ARG;
+    lct_plan p = new (std::nothrow) lct_plan_s();
+    if (!p) return LCT_ERR_OOM;
+    p->dtype = dtype;
+    p->is_batch = is_batch;
+    p->count = count;
+    p->N.assign(N, N + count);
+    p->abcd.assign(abcd, abcd + 8 * count);
+    p->desc.resize(count);
+    p->N0 = N[0];
+    for (int64_t s = 0; s < count; ++s) {
+        if (offsets && offsets[s] < 0) { delete p; return LCT_ERR_ARG; }
+        lct_status st = make_desc(N[s], abcd + 8 * s, offsets ? offsets[s] : 0, &p->desc[s]);
+        if (st != LCT_OK) { delete p; return st; }
+        if (N[s] != p->N0) p->N0 = 0;
+    }
+    *out = p;
+    return LCT_OK;
+}
+
+// Plain FP64 path: chirp kernel -> cuFFT Z2Z (forward) -> chirp+scale kernel.
+lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int desc_step,
+                     cudaStream_t stream) {
+    int64_t N = p->N0;
+    int log2n = p->desc[0].log2n;
+    size_t need = (size_t)count * (size_t)N * 16;
+    if (need > p->work_bytes) {
+        cudaFree(p->d_work);
+        p->d_work = nullptr;
+        p->work_bytes = 0;
+        if (cudaMalloc(&p->d_work, need) != cudaSuccess) return LCT_ERR_OOM;
+        p->work_bytes = need;
+    }
+    if (!p->fft_valid || p->fft_n != N || p->fft_batch != count) {
+        if (p->fft_valid) cufftDestroy(p->fft);
+        p->fft_valid = false;
+        int n = (int)N;
+        if (cufftPlanMany(&p->fft, 1, &n, nullptr, 1, n, nullptr, 1, n, CUFFT_Z2Z, (int)count) !=
+            CUFFT_SUCCESS)
+            return LCT_ERR_CUDA;
+        p->fft_valid = true;
+        p->fft_n = N;
+        p->fft_batch = count;
+    }
+    if (cufftSetStream(p->fft, stream) != CUFFT_SUCCESS) return LCT_ERR_CUDA;
+    lct_status st = from_cuda(lct_launch_plain_pre(p->dtype, log2n, in, p->d_work, p->d_desc,
+                                                   desc_step, count, stream));
+    if (st != LCT_OK) return st;
+    cufftDoubleComplex* w = (cufftDoubleComplex*)p->d_work;
+    if (cufftExecZ2Z(p->fft, w, w, CUFFT_FORWARD) != CUFFT_SUCCESS) return LCT_ERR_CUDA;
+    return from_cuda(lct_launch_plain_post(p->dtype, log2n, p->d_work, out, p->d_desc, desc_step,
+                                           count, stream));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lct_status lct_plan_create(lct_plan* out, int64_t N, double a, double b, double c, double d,
+                           lct_dtype dtype) {
+    double p[8] = {a, 0.0, b, 0.0, c, 0.0, d, 0.0};
+    return new_plan(out, dtype, 1, &N, p, nullptr, false);
+}
+
+lct_status lct_plan_create_complex(lct_plan* out, int64_t N, const double abcd_reim[8],
+                                   lct_dtype dtype) {
+    if (!abcd_reim) return LCT_ERR_ARG;
+    return new_plan(out, dtype, 1, &N, abcd_reim, nullptr, false);
+}
+
+lct_status lct_plan_create_batch(lct_plan* out, int64_t count, const int64_t* N,
+                                 const double* abcd_reim, const int64_t* offsets,
+                                 lct_dtype dtype) {
+    if (!N || !abcd_reim || !offsets) return LCT_ERR_ARG;
+    return new_plan(out, dtype, count, N, abcd_reim, offsets, true);
+}
+
+lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
+    if (!plan) return LCT_ERR_ARG;
+    switch (precision) {
+        case LCT_PREC_NATIVE:
+        case LCT_PREC_PLAIN64:
+            plan->prec = precision;
+            return LCT_OK;
+        case LCT_PREC_SPLIT_BF16:
+        case LCT_PREC_SPLIT_FP16:
+        case LCT_PREC_FP16:
+            return LCT_ERR_UNSUPPORTED;
+        default:
+            return LCT_ERR_ARG;
+    }
+}
+
+lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
+                       lct_stream_t stream_) {
+    if (!plan) return LCT_ERR_ARG;
+    if (batch < 0) return LCT_ERR_ARG;
+    if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
+    if (batch == 0) return LCT_OK;
+    lct_status st = check_ptr(in, plan->dtype);
+    if (st != LCT_OK) return st;
+    st = check_ptr(out, plan->dtype);
+    if (st != LCT_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    std::lock_guard<std::mutex> g(plan->mu);
+    st = ensure_device(plan);
+    if (st != LCT_OK) return st;
+    int desc_step = plan->is_batch ? 1 : 0;
+    if (plan->N0 == 0) return LCT_ERR_UNSUPPORTED;     // ragged batch: not yet
+    const lct_desc& D0 = plan->desc[0];
+    if (plan->is_batch) {
+        for (const lct_desc& D : plan->desc)
+            if (D.kind != D0.kind) return LCT_ERR_UNSUPPORTED;
+    }
+    int log2n = D0.log2n;
+    if (D0.kind == LCT_KIND_DIAG)
+        return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
+                                         batch, stream));
+    if (plan->prec == LCT_PREC_PLAIN64) {
+        if (plan->is_batch) {
+            // the plain path assumes contiguous rows
+            for (int64_t s = 0; s < plan->count; ++s)
+                if (plan->desc[s].offset != s * plan->N0) return LCT_ERR_UNSUPPORTED;
+        }
+        return run_plain(plan, in, out, batch, desc_step, stream);
+    }
+    if (!lct_fused_supported(plan->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
+    return from_cuda(lct_launch_fused(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
+                                      batch, stream));
+}
+
+lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
+                        int64_t batch, lct_dtype dtype, lct_stream_t stream) {
+    cplx z(z_re, z_im);
+    double az = std::abs(z);
+    if (!std::isfinite(az) || az == 0.0 || az > 1.0 + 1e-15) return LCT_ERR_ARG;
+    if (ilog2_exact(N) < 0) return LCT_ERR_N;
+    if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
+    double p[8];
+    double frft_scale_abs;
+    double frft_scale_turns;
+    cplx one_minus_z2 = 1.0 - z * z;
+    if (one_minus_z2 == cplx(0.0, 0.0)) {
+        // z = +-1: F_z = sqrt(2 pi) times the identity / the parity on y_j = x_j / z,
+        // which is the b = 0 branch with d = z, scaled by sqrt(2 pi)/sqrt(d).
+        cplx d = z;
+        p[0] = d.real(); p[1] = 0.0; p[2] = 0.0; p[3] = 0.0;
+        p[4] = 0.0; p[5] = 0.0; p[6] = d.real(); p[7] = 0.0;
+        cplx s = std::sqrt(2.0 * M_PI) / std::sqrt(d);
+        frft_scale_abs = std::abs(s);
+        frft_scale_turns = std::arg(s) / (2.0 * M_PI);
+    } else {
+        cplx zi = 1.0 / z;
+        cplx a = (z + zi) / 2.0;
+        cplx b = (zi - z) / cplx(0.0, 2.0);
+        cplx c = cplx(0.0, 1.0) * (zi - z) / 2.0;
+        p[0] = a.real(); p[1] = a.imag(); p[2] = b.real(); p[3] = b.imag();
+        p[4] = c.real(); p[5] = c.imag(); p[6] = a.real(); p[7] = a.imag();
+        // F_z = sqrt(2/(1-z^2)) sqrt(2 pi i b) LCT: multiply the LCT prefactor.
+        cplx s = std::sqrt(2.0 / one_minus_z2) * std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
+        frft_scale_abs = std::abs(s);
+        frft_scale_turns = std::arg(s) / (2.0 * M_PI);
+    }
+    lct_plan plan = nullptr;
+    // The mapped parameters satisfy ad - bc = 1 up to rounding.
+    lct_status st = new_plan(&plan, dtype, 1, &N, p, nullptr, false);
+    if (st != LCT_OK) return st;
+    plan->desc[0].scale *= frft_scale_abs;
+    plan->desc[0].out_c += double_to_turns64(frft_scale_turns);
+    st = lct_execute(plan, in, out, batch, stream);
+    // Free the plan's device state only after the stream has consumed it.
+    if (st == LCT_OK && plan->device >= 0) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = LCT_ERR_CUDA;
+    }
+    lct_plan_destroy(plan);
+    return st;
+}
+
+lct_status lct_output_grid(lct_plan plan, int64_t index, double* y_reim, double* rho) {
+    if (!plan || !y_reim || index < 0 || index >= plan->count) return LCT_ERR_ARG;
+    int64_t N = plan->N[index];
+    const double* p = plan->abcd.data() + 8 * index;
+    cplx b(p[2], p[3]), c(p[4], p[5]), d(p[6], p[7]);
+    for (int64_t j = 0; j < N; ++j) {
+        double m = (double)(2 * j - N + 1);
+        double x = M_PI * m / (2.0 * std::sqrt(2.0 * (double)N));
+        cplx y;
+        double r;
+        if (b == cplx(0.0, 0.0)) {
+            y = x / d;
+            r = -(c / d).imag() * M_PI * M_PI * m * m / (16.0 * (double)N);
+        } else {
+            y = 4.0 * b * x / M_PI;
+            r = -(b * d).imag() * m * m / (double)N;
+        }
+        y_reim[2 * j] = y.real();
+        y_reim[2 * j + 1] = y.imag();
+        if (rho) rho[j] = r;
+    }
+    return LCT_OK;
+}
+
+lct_status lct_input_grid(int64_t N, double* x) {
+    if (!x) return LCT_ERR_ARG;
+    if (ilog2_exact(N) < 0) return LCT_ERR_N;
+    for (int64_t k = 0; k < N; ++k)
+        x[k] = M_PI * (double)(2 * k - N + 1) / (2.0 * std::sqrt(2.0 * (double)N));
+    return LCT_OK;
+}
+
+lct_status lct_plan_phase_turns(lct_plan plan, int64_t index, uint64_t out[5]) {
+    if (!plan || !out || index < 0 || index >= plan->count) return LCT_ERR_ARG;
+    const lct_desc& D = plan->desc[index];
+    out[0] = D.in_hi;
+    out[1] = D.in_lo;
+    out[2] = D.out_hi;
+    out[3] = D.out_lo;
+    out[4] = D.out_c;
+    return LCT_OK;
+}
+
+lct_status lct_device_status(lct_plan plan, lct_stream_t stream) {
+    if (!plan) return LCT_ERR_ARG;
+    std::lock_guard<std::mutex> g(plan->mu);
+    if (plan->device < 0) return LCT_OK;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LCT_ERR_CUDA;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, plan->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LCT_ERR_CUDA;
+    if (v != LCT_DEV_OK) {
+        cudaMemset(plan->d_status, 0, sizeof(int32_t));
+        return v == LCT_DEV_TIMEOUT ? LCT_ERR_TIMEOUT : LCT_ERR_DEVICE;
+    }
+    return LCT_OK;
+}
+
+lct_status lct_plan_destroy(lct_plan plan) {
+    if (!plan) return LCT_ERR_ARG;
+    release_device(plan);
+    delete plan;
+    return LCT_OK;
+}
+
+const char* lct_status_string(lct_status s) {
+    switch (s) {
+        case LCT_OK: return "ok";
+        case LCT_ERR_ARG: return "invalid argument";
+        case LCT_ERR_N: return "N must be a power of two in [2, 65536]";
+        case LCT_ERR_NOT_SYMPLECTIC: return "parameters do not satisfy ad - bc = 1";
+        case LCT_ERR_DTYPE: return "unknown dtype";
+        case LCT_ERR_ALIGN: return "pointer not aligned to the sample size";
+        case LCT_ERR_OOM: return "out of device memory";
+        case LCT_ERR_CUDA: return "CUDA runtime or cuFFT error";
+        case LCT_ERR_DEVICE: return "a kernel recorded a per-item error";
+        case LCT_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case LCT_ERR_UNSUPPORTED: return "combination not supported";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Internal definitions shared by the host library and the CUDA kernels.
+//
+// Per-signal descriptor.  The transform of one signal (Sec. 3, Algorithm,
+// with the forward-sign DFT) is, for k, j = 0..N-1 and m = 2k - N + 1:
+//
+//   u_k = e^{2 pi i [phi_in m_k^2 + (N-1) k / (2N)]} e^{-decay m_k^2} f_k
+//   U   = DFT_N(u)          (forward sign e^{-2 pi i jk/N})
+//   G_j = scale * e^{2 pi i [phi_out m_j^2 + (N-1) j / (2N) + c_out]} U_j
+//
+// with phi_in  = Re(beta_in)/(2 pi),  beta_in  = a pi^2 / (16 b N)   (= a x_k^2/(2b) / m_k^2)
+//      phi_out = Re(beta_out)/(2 pi), beta_out = b d / N            (= d y_j^2/(2b) / m_j^2)
+//      decay   = Im(beta_in)
+//      scale * e^{2 pi i c_out} = dx e^{-i pi (N-1)^2 / (2N)} / sqrt(2 pi i b),  dx = pi/sqrt(2N).
+// phi_in and phi_out are 128-bit turn fractions (hi, lo words): the phase of
+// element m is the wrapped product phi * m^2 (m^2 < 2^32), which is exact to
+// 2^-96 turns; FP32 kernels use the top 64 bits only (error <= 2^-32 turns).
+// c_out is a 64-bit turn fraction.  The centring phases (N-1)k/(2N) are exact
+// dyadic fractions and are formed in the kernels from k and N.
+//
+// kind == LCT_KIND_DIAG (b == 0): G_j = scale e^{2 pi i [phi_out m_j^2 + c_out]} f_j
+// with phi_out = Re(c/d) pi / (32 N) (the phase c x_j^2/(2d)), scale e^{2 pi i c_out} = sqrt(d).
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1 };
+enum { LCT_FLAG_DECAY = 1 };
+
+struct __align__(16) lct_desc {
+    uint64_t in_hi, in_lo;    // phi_in  (128-bit turn fraction)
+    uint64_t out_hi, out_lo;  // phi_out (128-bit turn fraction)
+    uint64_t out_c;           // constant output turn offset (64-bit fraction)
+    int64_t offset;           // element offset of the signal in in/out
+    double scale;             // |prefactor|
+    double decay;             // Im(beta_in) (pre-chirp magnitude e^{-decay m^2})
+    int32_t log2n;
+    int32_t kind;
+    int32_t flags;
+    int32_t pad;
+};
+static_assert(sizeof(lct_desc) == 80, "descriptor layout");
+
+// Device status word values (first error wins).
+enum { LCT_DEV_OK = 0, LCT_DEV_BAD_DESC = 1, LCT_DEV_TIMEOUT = 2 };
+
+// ---- kernel launchers (defined in the .cu files) ---------------------------
+// Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
+// desc_step = 0: one descriptor for all `count` signals (signal s at s*N);
+// desc_step = 1: desc[s] for signal s (its own offset).
+// dtype: 0 = complex64 (FP32 arithmetic), 1 = complex128 (FP64 arithmetic).
+cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
+                             const lct_desc* desc, int desc_step, int64_t count,
+                             cudaStream_t stream);
+bool lct_fused_supported(int dtype, int log2n);
+
+// Diagonal branch (b == 0) for `count` signals of N = 2^log2n.
+cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,
+                            const lct_desc* desc, int desc_step, int64_t count,
+                            cudaStream_t stream);
+
+// Plain FP64 baseline pieces.  work: complex128 [count][N].
+cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,
+                                 const lct_desc* desc, int desc_step, int64_t count,
+                                 cudaStream_t stream);
+cudaError_t lct_launch_plain_post(int dtype, int log2n, const void* work, void* out,
+                                  const lct_desc* desc, int desc_step, int64_t count,
+                                  cudaStream_t stream);

@@ -1,0 +1,154 @@
+"""The C-ABI library on the CPU: it loads, exports every declared symbol, and
+its host-side logic (validation, grids, exact phase constants) is right.
+No compute call is made here (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_0912_1379_gb300 as lct
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    lct.build()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "lct_execute" in names and "frft_execute" in names and "lct_plan_create" in names
+    lib = ctypes.CDLL(lct.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    for s in range(len(lct.STATUS)):
+        assert lct.lct_status_string(s) not in ("", "unknown status")
+
+
+def test_input_grid_matches_oracle_nodes():
+    for N in [2, 16, 1024, 65536]:
+        x = lct.lct_input_grid(N)
+        assert np.allclose(x, O.nodes(N), rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [0, 1, 3, 100, 131072, -4])
+def test_bad_N(N):
+    with pytest.raises(lct.LctError) as e:
+        lct.lct_plan_create(N, 1.0, 2.0, 0.5, 2.0)
+    assert e.value.status == 2
+
+
+def test_not_symplectic_and_dtype():
+    with pytest.raises(lct.LctError) as e:
+        lct.lct_plan_create(64, 1.0, 2.0, 0.6, 2.0)
+    assert e.value.status == 3
+    with pytest.raises(lct.LctError) as e:
+        lct.lct_plan_create(64, 1.0, 2.0, 0.5, 2.0, dtype=7)
+    assert e.value.status == 4
+    with pytest.raises(lct.LctError) as e:
+        lct.lct_plan_create(64, float("nan"), 2.0, 0.5, 2.0)
+    assert e.value.status == 1
+
+
+def test_execute_validation_without_gpu():
+    p = lct.lct_plan_create(64, 1.0, 2.0, 0.5, 2.0)
+    try:
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute(p, 0, 0, 1, stream=0)
+        assert e.value.status == 1
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute(p, 4, 4, 1, stream=0)          # not 8-byte aligned
+        assert e.value.status == 5
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute(p, 64, 64, -1, stream=0)
+        assert e.value.status == 1
+        lct.lct_execute(p, 64, 64, 0, stream=0)             # batch 0: no-op, no device touched
+    finally:
+        lct.lct_plan_destroy(p)
+    bp = lct.lct_plan_create_batch([64, 64], [[1, 2, 0.5, 2], [0, 1, -1, 0]], [0, 64])
+    try:
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute(bp, 64, 64, 3, stream=0)
+        assert e.value.status == 1
+    finally:
+        lct.lct_plan_destroy(bp)
+
+
+@pytest.mark.parametrize("z", [0.0, 1.5, 2j, complex(float("nan"), 0)])
+def test_frft_bad_z(z):
+    with pytest.raises(lct.LctError) as e:
+        lct.frft_execute(64, z, 64, 64, 1, stream=0)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("abcd", [(1.0, 2.0, 0.5, 2.0), (0.0, 1.0, -1.0, 0.0), (2.0, 0.0, 0.3, 0.5),
+                                  (0.3 + 0.1j, 0.5 - 0.7j, None, 1.1 + 0.2j)])
+def test_output_grid_matches_oracle(abcd):
+    a, b, c, d = abcd
+    if c is None:
+        c = (a * d - 1) / b
+    N = 128
+    p = lct.Plan.create(N, a, b, c, d)
+    try:
+        y, rho = lct.lct_output_grid(p.handle, 0, N)
+    finally:
+        p.destroy()
+    yo = O.output_grid(N, [a, b, c, d])
+    f = np.ones(N, dtype=np.complex128)
+    _, rho_o = O.lct(f, [a, b, c, d], return_rho=True)
+    assert np.allclose(y, yo, rtol=1e-14, atol=1e-13)
+    assert np.allclose(rho, rho_o, rtol=1e-12, atol=1e-12)
+
+
+def _turns_err(q, exact, bits):
+    """signed difference (in units of 2^-bits turns) between a fixed-point
+    fraction q and an exact mpmath turn count, modulo one turn."""
+    import mpmath
+    mod = 1 << bits
+    e = int(mpmath.floor((exact - mpmath.floor(exact)) * mod + mpmath.mpf(0.5))) % mod
+    dlt = (q - e) % mod
+    return dlt - mod if dlt >= mod // 2 else dlt
+
+
+@pytest.mark.parametrize("N,abcd", [(256, (np.cos(0.7), np.sin(0.7), -np.sin(0.7), np.cos(0.7))),
+                                    (65536, (1.7, 0.21, (1.7 * -1.3 - 1) / 0.21, -1.3)),
+                                    (1024, (1.0, 100.0, 0.0, 1.0)),
+                                    (64, (0.3, -1.9, (0.3 * 0.4 - 1) / -1.9, 0.4))])
+def test_phase_constants_exact(N, abcd):
+    """The 128-bit turn fractions equal the exactly computed phases of the
+    FP64 parameters to better than 2^-100 turns (mpmath, 60 digits)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    a, b, c, d = abcd
+    p = lct.lct_plan_create(N, a, b, c, d)
+    try:
+        in_hi, in_lo, out_hi, out_lo, out_c = lct.lct_plan_phase_turns(p)
+    finally:
+        lct.lct_plan_destroy(p)
+    A, B, D = mpmath.mpf(a), mpmath.mpf(b), mpmath.mpf(d)
+    t_in = A * mpmath.pi / (32 * B * N)               # a x^2/(2b) per m^2, in turns
+    t_out = B * D / (2 * mpmath.pi * N)               # d y^2/(2b) per m^2, in turns
+    assert abs(_turns_err((in_hi << 64) | in_lo, t_in, 128)) < 2 ** 28
+    assert abs(_turns_err((out_hi << 64) | out_lo, t_out, 128)) < 2 ** 28
+    # output constant: -(N-1)^2/(4N) + arg(dx / sqrt(2 pi i b)) / (2 pi)
+    dx = mpmath.pi / mpmath.sqrt(2 * N)
+    pre = dx / mpmath.sqrt(2j * mpmath.pi * B)
+    t_c = -mpmath.mpf((N - 1) ** 2) / (4 * N) + mpmath.arg(pre) / (2 * mpmath.pi)
+    assert abs(_turns_err(out_c, t_c, 64)) < 2 ** 14

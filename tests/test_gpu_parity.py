@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances (relative L2 per signal, the maximum over signals must pass):
+  FP64 paths (complex128, fused and plain)   1e-12
+  FP32 fused path (complex64)                1e-5
+  plain FP64 path with complex64 I/O         1e-6 (output rounded to FP32)
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from conftest import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_0912_1379_gb300 as lct  # noqa: E402
+
+TOL64, TOL32 = 1e-12, 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lct.build()
+    torch.cuda.set_device(0)
+
+
+def to_dev(f, dtype):
+    return torch.from_numpy(np.ascontiguousarray(f.astype(dtype))).cuda()
+
+
+def run(plan, f, dtype, batch=None, inplace=False):
+    x = to_dev(f, dtype)
+    out = x if inplace else torch.empty_like(x)
+    n = f.shape[0] if batch is None else batch
+    lct.lct_execute(plan, x, out, n)
+    torch.cuda.synchronize()
+    assert lct.lct_device_status(plan) == 0
+    return out.cpu().numpy()
+
+
+def rot(t):
+    return (np.cos(t), np.sin(t), -np.sin(t), np.cos(t))
+
+
+# --------------------------------------------------------------------------
+# config 0: N = 256, complex128, rotation 0.7, polynomial + psi_0..psi_10
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [lct.LCT_PREC_NATIVE, lct.LCT_PREC_PLAIN64])
+def test_config0_fp64(prec):
+    N = 256
+    x = O.nodes(N)
+    f = W.config0_signals(x)
+    abcd = W.config0_params()
+    p = lct.Plan.create(N, *abcd, dtype=lct.LCT_C128).set_precision(prec)
+    try:
+        G = run(p.handle, f, np.complex128)
+    finally:
+        p.destroy()
+    ref = O.lct(f, abcd)
+    assert rel_l2(G, ref).max() < TOL64
+
+
+# --------------------------------------------------------------------------
+# every supported N, both precisions, ragged batch counts
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("log2n", list(range(1, 13)))
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_every_size(log2n, dtype):
+    N = 1 << log2n
+    count = 37 if N <= 1024 else 5           # not a multiple of the signals per CTA
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=100 + log2n, dtype=np.complex128)
+    abcd = (0.37, -1.3, (0.37 * 0.8 - 1) / -1.3, 0.8)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.create(N, *abcd, dtype=code)
+    try:
+        G = run(p.handle, f.astype(dtype), dtype)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+    tol = TOL32 if dtype == np.complex64 else TOL64
+    assert rel_l2(G, ref).max() < tol
+
+
+# --------------------------------------------------------------------------
+# per-signal parameters (batch plan), generator G1
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,count,seed", [(1024, 512, W.SEED_UNIFORM_1024), (4096, 48, 77)])
+def test_uniform_batch_per_signal_params(N, count, seed):
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=seed, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=lct.LCT_C64)
+    try:
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(np.complex128), params)
+    err = rel_l2(G, ref)
+    assert err.max() < TOL32
+
+
+def test_in_place_equals_out_of_place():
+    N, count = 4096, 6
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=5, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N)
+    try:
+        a = run(p.handle, f, np.complex64)
+        b = run(p.handle, f, np.complex64, inplace=True)
+    finally:
+        p.destroy()
+    assert np.array_equal(a, b)
+
+
+def test_plain64_complex64_io():
+    N, count = 1024, 16
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=9, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N).set_precision(lct.LCT_PREC_PLAIN64)
+    try:
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(np.complex128), params)
+    assert rel_l2(G, ref).max() < 1e-6
+
+
+# --------------------------------------------------------------------------
+# b = 0 branch, complex parameters, fractional transform
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_b_zero(dtype):
+    N = 512
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, 7, seed=3, dtype=np.complex128)
+    abcd = (1 / 1.7, 0.0, -0.9, 1.7)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.create(N, *abcd, dtype=code)
+    try:
+        G = run(p.handle, f.astype(dtype), dtype)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+    assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64)
+
+
+@pytest.mark.parametrize("z", [0.5 + 0.3j, 0.9 * np.exp(2.0j), np.exp(-0.7j), 1.0, -1.0])
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_frft(z, dtype):
+    N = 256
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, 5, seed=11, dtype=np.complex128)
+    f = f.astype(dtype)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    xin = to_dev(f, dtype)
+    out = torch.empty_like(xin)
+    lct.frft_execute(N, z, xin, out, f.shape[0], code)
+    torch.cuda.synchronize()
+    G = out.cpu().numpy()
+    if abs(1 - z * z) == 0:
+        ref = np.sqrt(2 * np.pi) * f.astype(np.complex128)     # F_{+-1} = sqrt(2 pi) I on y = x/z
+    else:
+        ref = O.frft(f.astype(np.complex128), z)
+    assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64)
+
+
+def test_complex_parameters_plan():
+    N = 1024
+    z = 0.6 * np.exp(1.2j)
+    abcd = O.abcd_of_z(z)
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, 4, seed=12, dtype=np.complex128)
+    p = lct.Plan.create(N, *[complex(v) for v in abcd], dtype=lct.LCT_C128)
+    try:
+        G = run(p.handle, f, np.complex128)
+        y, rho = lct.lct_output_grid(p.handle, 0, N)
+    finally:
+        p.destroy()
+    ref, rho_o = O.lct(f, abcd, return_rho=True)
+    assert rel_l2(G, ref).max() < TOL64
+    assert np.allclose(rho, rho_o[0], rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the throughput workload at full size, in the launch configuration the
+# benchmark times: 16384 signals x N = 4096, complex64, per-signal params
+# --------------------------------------------------------------------------
+def test_full_size_uniform_4096():
+    N, count = 4096, 16384
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N)
+    try:
+        xin = to_dev(f, np.complex64)
+        out = torch.empty_like(xin)
+        lct.lct_execute(p.handle, xin, out, count)
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        # property at every signal: scaled Parseval ||G||^2 dy = ||f||^2 dx, dy = 4|b| dx / pi
+        nf = torch.linalg.vector_norm(xin.to(torch.complex128), dim=1) ** 2
+        ng = torch.linalg.vector_norm(out.to(torch.complex128), dim=1) ** 2
+        b = torch.from_numpy(np.abs(params[:, 1])).cuda()
+        ratio = (ng * 4 * b / np.pi / nf).cpu().numpy()
+        assert np.abs(ratio - 1).max() < 2e-5
+        idx = np.arange(0, count, 256)                           # 64 sampled signals
+        G = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    finally:
+        p.destroy()
+    ref = O.lct(f[idx].astype(np.complex128), params[idx])
+    assert rel_l2(G, ref).max() < TOL32
