@@ -144,6 +144,32 @@ lct_status lct_device_status(lct_plan plan, lct_stream_t stream);
 
 lct_status lct_plan_destroy(lct_plan plan);
 
+/* No counterpart in the paper: an extra entry point for callers that cannot
+ * call cudaMalloc -- a process whose device memory is fully reserved up front
+ * by its own pool allocator, or a latency-critical caller that must not hit
+ * the implicit device synchronisation of cudaMalloc/cudaFree.
+ * Computes the same transform as a plan from lct_plan_create(N, a, b, c, d,
+ * dtype) with LCT_PREC_PLAIN64 (FP64 chirp, FP64 DFT, FP64 chirp + scale;
+ * complex64 or complex128 samples in and out), but allocates nothing: no
+ * plan, no cudaMalloc/cudaFree, no cuFFT plan, no other allocating library
+ * call.  The FP64 intermediate lives in one static device array of
+ * LCT_NOALLOC_MAX_POINTS complex128 samples (32 MiB) that every GPU which
+ * loads the library holds until the process exits.
+ * Limits: N a power of two in [2, LCT_NOALLOC_MAX_N], else LCT_ERR_N;
+ * batch * N <= LCT_NOALLOC_MAX_POINTS, else LCT_ERR_ARG (nothing is run).
+ * The first call on a device looks up the array's device address and sets
+ * the DFT kernel's shared-memory limit (once per device); make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  No state carries over between calls.
+ * in/out as lct_execute (device buffers, in == out allowed); asynchronous on
+ * `stream`. */
+#define LCT_NOALLOC_MAX_N 4096
+#define LCT_NOALLOC_MAX_POINTS (1 << 21)
+lct_status lct_execute_noalloc(int64_t N, double a, double b, double c, double d,
+                               lct_dtype dtype, const void* in, void* out, int64_t batch,
+                               lct_stream_t stream);
+
 const char* lct_status_string(lct_status status);
 
 #ifdef __cplusplus

@@ -69,6 +69,7 @@ def _load():
             "lct_plan_phase_turns": [vp, i64, up],
             "lct_device_status": [vp, vp],
             "lct_plan_destroy": [vp],
+            "lct_execute_noalloc": [i64, f64, f64, f64, f64, i32, vp, vp, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -202,6 +203,19 @@ def lct_plan_destroy(plan: int) -> None:
 
 def lct_status_string(status: int) -> str:
     return _status_string(status)
+
+
+LCT_NOALLOC_MAX_N = 4096
+LCT_NOALLOC_MAX_POINTS = 1 << 21
+
+
+def lct_execute_noalloc(N: int, a: float, b: float, c: float, d: float, inp, out, batch: int,
+                        dtype: int = LCT_C64, stream=None) -> None:
+    """FP64 transform that allocates no device memory (static 32 MiB work
+    array; batch * N <= LCT_NOALLOC_MAX_POINTS, N <= LCT_NOALLOC_MAX_N).
+    Calls that overlap on the GPU race on the shared array."""
+    _check(_load().lct_execute_noalloc(N, a, b, c, d, dtype, _ptr(inp), _ptr(out), batch,
+                                       _stream_handle(stream)), "lct_execute_noalloc")
 
 
 # ---------------------------------------------------------------------------

@@ -184,6 +184,10 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
 
 }  // namespace
 
+int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {
+    return (int)make_desc(N, p, offset, D);
+}
+
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------

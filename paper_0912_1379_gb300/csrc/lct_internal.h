@@ -43,6 +43,11 @@ static_assert(sizeof(lct_desc) == 80, "descriptor layout");
 // Device status word values (first error wins).
 enum { LCT_DEV_OK = 0, LCT_DEV_BAD_DESC = 1, LCT_DEV_TIMEOUT = 2 };
 
+// Host: the descriptor of one N-point signal with parameters
+// p = {a_re, a_im, b_re, b_im, c_re, c_im, d_re, d_im} (validates like
+// lct_plan_create; returns an lct_status value).
+int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D);
+
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 // Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
 // desc_step = 0: one descriptor for all `count` signals (signal s at s*N);
