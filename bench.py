@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2"],
+                    help="fused kernel variant (auto: the library's autotuner)")
     return ap.parse_args()
 
 
@@ -260,6 +262,12 @@ def main():
     def step():
         plan.execute(d_in, d_out, count, stream)
 
+    if args.variant == "auto":
+        variant = plan.autotune(d_in, d_out, count, stream)
+    else:
+        variant = int(args.variant)
+        plan.set_variant(variant)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -305,7 +313,8 @@ def main():
     achieved = n_points * BYTES_PER_POINT / (ms_per_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_per_launch(n_points),
-                "kernel": "k_xft_fused<12, float> (N=4096, complex64)",
+                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>"}[variant]
+                          + " (N=4096, complex64)",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}
 
@@ -330,6 +339,7 @@ def main():
         # release the plain path's workspace
         plan.destroy()
         plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+        plan.set_variant(variant)
         step()
         torch.cuda.synchronize()
 
@@ -375,6 +385,7 @@ def main():
             "config": {"workload": "uniform batch %d x N=%d complex64, G1 per-signal (a,b,c,d), seed %d"
                                    % (count, N, W.SEED_UNIFORM_4096),
                        "signals_per_gpu": count, "N": N, "transforms_per_s": value / N,
+                       "kernel_variant": variant,
                        "l2": "inputs larger than L2 (512 MiB per buffer), no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,

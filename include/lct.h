@@ -108,6 +108,28 @@ lct_status lct_plan_create_batch(lct_plan* out, int64_t count, const int64_t* N,
 
 lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
 
+/* Kernel variants of the fused path (LCT_PREC_NATIVE), chosen per plan:
+ *  0  one CTA per group of signals, grid = number of groups (default);
+ *  1  persistent CTAs that prefetch the next group into shared memory with
+ *     bulk asynchronous copies while the current one is transformed
+ *     (complex64, N = 256 .. 8192, 16-byte aligned signal starts; other
+ *     plans fall back to variant 0), twiddles read from the table;
+ *  2  as 1 with twiddles computed in registers.
+ * LCT_ERR_ARG for an unknown variant.  Host-only. */
+lct_status lct_plan_set_variant(lct_plan plan, int variant);
+lct_status lct_plan_get_variant(lct_plan plan, int* variant);
+
+/* Autotuner: run every variant that can execute this plan on the given
+ * buffers (2 warm-up and 5 timed launches each, CUDA events on `stream`,
+ * synchronising), keep the fastest in the plan and in a process-wide cache
+ * keyed by (GPU name, dtype, N, precision).  If the environment variable
+ * LCT_AUTOTUNE_CACHE names a file, it is read first (lines
+ * "gpu|dtype|log2n|variant") and new results are appended.  `out` is
+ * overwritten.  Plans created later with a cached key start with the cached
+ * variant. */
+lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t batch,
+                             lct_stream_t stream);
+
 /* Apply the plan.  in/out: device buffers in the plan's dtype.  For a plan
  * from lct_plan_create[_complex], `batch` signals of N samples, row-major.
  * For a batch plan, `batch` must equal its count.  in == out is allowed.

@@ -70,6 +70,9 @@ def _load():
             "lct_device_status": [vp, vp],
             "lct_plan_destroy": [vp],
             "lct_execute_noalloc": [i64, f64, f64, f64, f64, i32, vp, vp, i64, vp],
+            "lct_plan_set_variant": [vp, i32],
+            "lct_plan_get_variant": [vp, ctypes.POINTER(i32)],
+            "lct_plan_autotune": [vp, vp, vp, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -154,6 +157,23 @@ def lct_plan_create_batch(N, abcd, offsets, dtype: int = LCT_C64) -> int:
 
 def lct_plan_set_precision(plan: int, precision: int) -> None:
     _check(_load().lct_plan_set_precision(plan, precision), "lct_plan_set_precision")
+
+
+def lct_plan_set_variant(plan: int, variant: int) -> None:
+    _check(_load().lct_plan_set_variant(plan, variant), "lct_plan_set_variant")
+
+
+def lct_plan_get_variant(plan: int) -> int:
+    v = ctypes.c_int()
+    _check(_load().lct_plan_get_variant(plan, ctypes.byref(v)), "lct_plan_get_variant")
+    return v.value
+
+
+def lct_plan_autotune(plan: int, inp, out, batch: int, stream=None) -> int:
+    """Time the kernel variants on these buffers; returns the chosen one."""
+    _check(_load().lct_plan_autotune(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
+           "lct_plan_autotune")
+    return lct_plan_get_variant(plan)
 
 
 def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
@@ -245,6 +265,13 @@ class Plan:
 
     def execute(self, inp, out, batch: int, stream=None) -> None:
         lct_execute(self.handle, inp, out, batch, stream)
+
+    def set_variant(self, variant: int) -> "Plan":
+        lct_plan_set_variant(self.handle, variant)
+        return self
+
+    def autotune(self, inp, out, batch: int, stream=None) -> int:
+        return lct_plan_autotune(self.handle, inp, out, batch, stream)
 
     def destroy(self) -> None:
         if self.handle:

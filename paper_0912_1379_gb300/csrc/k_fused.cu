@@ -1,126 +1,42 @@
 // Fused XFT kernel: pre-chirp -> N-point DFT -> post-chirp + scale, with the
 // whole signal resident in registers and shared memory, so each sample is
 // read from HBM once and written once (Sec. 3, Algorithm, steps 1-3; the DFT
-// with the forward sign, see include/lct.h).
-//
-// DFT: self-sorting Stockham formulation.  Every thread owns E = 16 samples
-// (E = N for N < 16), T = N/E threads per signal.  Pass p has radix R_p
-// (first pass 2^(log2N mod 4) or 16, then 16) and sub-length Ns_p (product
-// of the previous radices).  In every pass thread i holds the samples
-// i + e T (e = 0..15) -- the coalesced pattern, so the first pass reads
-// global memory directly and the last pass writes it directly -- applies
-// twiddles e^{-2 pi i j k / (Ns R)} (k = i' mod Ns) and a radix-R DFT in
-// registers, and writes sample j of virtual thread i' to position
-// (i' - k) R + k + j Ns.  Shared memory is padded by one slot per 16 so
-// that every exchange is free of bank conflicts.
-#include "xft_common.cuh"
+// with the forward sign, see include/lct.h).  The DFT is the Stockham engine
+// of xft_engine.cuh; one CTA holds SPC signals (several for small N).
+// Sizes: N = 2 .. 16384 (complex64), N = 2 .. 8192 (complex128).
+#include "xft_engine.cuh"
+#include "xft_async.cuh"
 
 namespace {
 
-constexpr int pass_count(int L) { return L >= 4 ? (L + 3) / 4 : 1; }
-constexpr int first_radix(int L) { return 1 << (L - 4 * (pass_count(L) - 1)); }
-__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+using namespace xft;
 
 template <int L>
-struct xft_shape {
-    static constexpr int N = 1 << L;
-    static constexpr int E = L >= 4 ? 16 : N;
-    static constexpr int T = N / E;
-    static constexpr int SPC = T >= 256 ? 1 : 256 / T;
+struct fused_shape {
+    static constexpr int T = shape<L>::T;
+    static constexpr int SPC = T >= 256 ? 1 : 256 / T;     // signals per CTA
     static constexpr int THREADS = T * SPC;
-    static constexpr int NP = N + (N >> 4);
-    static constexpr int P = pass_count(L);
 };
 
-template <int L, int p>
-struct pass_info {
-    static constexpr int RADIX = p == 0 ? first_radix(L) : 16;
-    static constexpr int NS = p == 0 ? 1 : first_radix(L) << (4 * (p - 1));
-    static constexpr int ns() { return NS; }
-};
-
-// e^{SGN 2 pi i k / M} (M a power of two, so 2k/M is exact).
-template <class R, int SGN>
-__device__ __forceinline__ cpx<R> twiddle_base(int k, int M) {
-    R s, c;
-    if constexpr (sizeof(R) == 4) sincospif((float)(2 * k) / (float)M, &s, &c);
-    else sincospi((double)(2 * k) / (double)M, &s, &c);
-    return {c, SGN < 0 ? -s : s};
+// Minimum resident CTAs per SM for __launch_bounds__: keeps FP32 kernels at
+// <= 64 registers (1024 resident threads fill the 64K register file) and
+// FP64 kernels at <= 128 (512 resident threads).
+template <int L, class R>
+constexpr int min_blocks() {
+    constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
+    return per_sm / fused_shape<L>::THREADS > 0 ? per_sm / fused_shape<L>::THREADS : 1;
 }
-
-// Twiddles + radix-R DFTs of one pass on the registers of thread i.
-template <int RADIX, int NS, int E, int T, int SGN, class R>
-__device__ __forceinline__ void butterflies(cpx<R>* v, int i) {
-    constexpr int V = E / RADIX;
-#pragma unroll
-    for (int vv = 0; vv < V; ++vv) {
-        cpx<R> u[RADIX];
-#pragma unroll
-        for (int j = 0; j < RADIX; ++j) u[j] = v[vv + j * V];
-        if (NS > 1) {
-            const int ip = i + vv * T;
-            const int k = ip & (NS - 1);
-            cpx<R> w[RADIX];
-            twiddle_powers<RADIX>(twiddle_base<R, SGN>(k, NS * RADIX), w);
-#pragma unroll
-            for (int j = 1; j < RADIX; ++j) u[j] = cmul(u[j], w[j]);
-        }
-        dft<RADIX, SGN>(u);
-#pragma unroll
-        for (int j = 0; j < RADIX; ++j) v[vv + j * V] = u[j];
-    }
-}
-
-template <int RADIX, int NS, int E, int T, class R>
-__device__ __forceinline__ void stockham_store(const cpx<R>* v, cpx<R>* buf, int i) {
-    constexpr int V = E / RADIX;
-#pragma unroll
-    for (int vv = 0; vv < V; ++vv) {
-        const int ip = i + vv * T;
-        const int k = ip & (NS - 1);
-        const int base = (ip - k) * RADIX + k;
-#pragma unroll
-        for (int j = 0; j < RADIX; ++j) buf[pad_idx(base + j * NS)] = v[vv + j * V];
-    }
-}
-
-template <int E, int T, class R>
-__device__ __forceinline__ void stockham_load(cpx<R>* v, const cpx<R>* buf, int i) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = buf[pad_idx(i + e * T)];
-}
-
-// Passes 1..P-1 (pass 0 is done by the caller right after the global load).
-template <int L, int p, int SGN, class R>
-struct run_passes {
-    __device__ __forceinline__ static void go(cpx<R>* v, cpx<R>* buf, int i) {
-        using S = xft_shape<L>;
-        using PP = pass_info<L, p - 1>;
-        using PI = pass_info<L, p>;
-        // results of pass p-1 -> shared memory
-        __syncthreads();
-        stockham_store<PP::RADIX, PP::NS, S::E, S::T>(v, buf, i);
-        __syncthreads();
-        stockham_load<S::E, S::T>(v, buf, i);
-        butterflies<PI::RADIX, PI::NS, S::E, S::T, SGN>(v, i);
-        run_passes<L, p + 1, SGN, R>::go(v, buf, i);
-    }
-};
-template <int L, int SGN, class R>
-struct run_passes<L, xft_shape<L>::P, SGN, R> {
-    __device__ __forceinline__ static void go(cpx<R>*, cpx<R>*, int) {}
-};
 
 // Pre-chirp e^{2 pi i [phi_in m^2 + (N-1) n/(2N)]} e^{-decay m^2} of sample n.
-template <int L, bool FAST>
+template <int L>
 __device__ __forceinline__ cpx<float> pre_chirp(const lct_desc& D, int n, bool decay) {
     constexpr uint32_t CEN = (uint32_t)(((1u << L) - 1u) << (31 - L));
     const uint32_t m2 = m_squared(n, 1 << L);
-    cpx<float> w = expi_turn32<FAST>(phase32(D.in_hi, m2) + (uint32_t)n * CEN);
+    cpx<float> w = expi_turn32<true>(phase32(D.in_hi, m2) + (uint32_t)n * CEN);
     if (decay) w = cscale(w, expf(-(float)D.decay * (float)m2));
     return w;
 }
-template <int L, bool FAST>
+template <int L>
 __device__ __forceinline__ cpx<double> pre_chirp64(const lct_desc& D, int n, bool decay) {
     constexpr uint64_t CEN = (uint64_t)(((1ull << L) - 1ull) << (63 - L));
     const uint32_t m2 = m_squared(n, 1 << L);
@@ -128,42 +44,45 @@ __device__ __forceinline__ cpx<double> pre_chirp64(const lct_desc& D, int n, boo
     if (decay) w = cscale(w, exp(-D.decay * (double)m2));
     return w;
 }
-template <int L, bool FAST>
+// Post-chirp e^{2 pi i [phi_out m^2 + (N-1) n/(2N) + c_out]} of sample n.
+template <int L>
 __device__ __forceinline__ cpx<float> post_chirp(const lct_desc& D, int n) {
     constexpr uint32_t CEN = (uint32_t)(((1u << L) - 1u) << (31 - L));
     const uint32_t m2 = m_squared(n, 1 << L);
     const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
-    return expi_turn32<FAST>(phase32(D.out_hi, m2) + (uint32_t)n * CEN + off);
+    return expi_turn32<true>(phase32(D.out_hi, m2) + (uint32_t)n * CEN + off);
 }
-template <int L, bool FAST>
+template <int L>
 __device__ __forceinline__ cpx<double> post_chirp64(const lct_desc& D, int n) {
     constexpr uint64_t CEN = (uint64_t)(((1ull << L) - 1ull) << (63 - L));
     const uint32_t m2 = m_squared(n, 1 << L);
     return expi_turn64(phase64(D.out_hi, D.out_lo, m2) + (uint64_t)n * CEN + D.out_c);
 }
 
-template <int L, class R, bool FAST>
+template <int L, class R>
 __device__ __forceinline__ cpx<R> pre_w(const lct_desc& D, int n, bool decay) {
-    if constexpr (sizeof(R) == 4) return pre_chirp<L, FAST>(D, n, decay);
-    else return pre_chirp64<L, FAST>(D, n, decay);
+    if constexpr (sizeof(R) == 4) return pre_chirp<L>(D, n, decay);
+    else return pre_chirp64<L>(D, n, decay);
 }
-template <int L, class R, bool FAST>
+template <int L, class R>
 __device__ __forceinline__ cpx<R> post_w(const lct_desc& D, int n) {
-    if constexpr (sizeof(R) == 4) return post_chirp<L, FAST>(D, n);
-    else return post_chirp64<L, FAST>(D, n);
+    if constexpr (sizeof(R) == 4) return post_chirp<L>(D, n);
+    else return post_chirp64<L>(D, n);
 }
 
-template <int L, class R, bool FAST>
-__global__ void __launch_bounds__(xft_shape<L>::THREADS)
+template <int L, class R>
+__global__ void __launch_bounds__(fused_shape<L>::THREADS, (min_blocks<L, R>()))
 k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
-            const lct_desc* __restrict__ desc, int desc_step, int64_t count) {
-    using S = xft_shape<L>;
+            const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+            const cpx<R>* __restrict__ tw) {
+    using S = shape<L>;
+    using F = fused_shape<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
     const int tid = threadIdx.x;
     const int sl = tid / S::T;
     const int i = tid - sl * S::T;
-    const int64_t sig = (int64_t)blockIdx.x * S::SPC + sl;
+    const int64_t sig = (int64_t)blockIdx.x * F::SPC + sl;
     const bool active = sig < count;
     const lct_desc D = desc[desc_step && active ? sig : 0];
     const int64_t base = desc_step ? D.offset : sig * (int64_t)S::N;
@@ -176,63 +95,221 @@ k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     for (int e = 0; e < S::E; ++e) {
         const int n = i + e * S::T;
         cpx<R> f = {R(0), R(0)};
-        if (active) f = in[base + n];
-        v[e] = cmul(f, pre_w<L, R, FAST>(D, n, decay));
+        if (active) f = ld_stream(in + base + n);
+        v[e] = cmul(f, pre_w<L, R>(D, n, decay));
     }
-    butterflies<pass_info<L, 0>::RADIX, pass_info<L, 0>::ns(), S::E, S::T, -1>(v, i);
-    run_passes<L, 1, -1, R>::go(v, buf, i);
+    dft_signal<L, -1>(v, buf, i, tw);
     // global store (sample i + e T) with the post-chirp and scale
     if (active) {
         const R sc = (R)D.scale;
 #pragma unroll
         for (int e = 0; e < S::E; ++e) {
             const int n = i + e * S::T;
-            out[base + n] = cscale(cmul(v[e], post_w<L, R, FAST>(D, n)), sc);
+            out[base + n] = cscale(cmul(v[e], post_w<L, R>(D, n)), sc);
         }
     }
 }
 
+// Persistent variant (complex64): each CTA loops over groups of SPC signals.
+// The next group's samples are brought into a shared-memory stage by bulk
+// asynchronous copies (cp.async.bulk, completing on an mbarrier) while the
+// current group is transformed, so HBM latency is hidden behind compute.
+// Requires 16-byte aligned signal starts (checked on the host).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
+
+template <int L>
+__device__ __forceinline__ void issue_group(const cpx<float>* in, const lct_desc* desc,
+                                            int desc_step, int64_t count, int64_t g,
+                                            cpx<float>* stage, uint64_t* bar) {
+    using S = shape<L>;
+    using F = fused_shape<L>;
+    uint32_t bytes = 0;
+    for (int s = 0; s < F::SPC; ++s)
+        if (g * F::SPC + s < count) bytes += S::N * (uint32_t)sizeof(cpx<float>);
+    xasync::mbar_arrive_expect_tx(bar, bytes);
+    for (int s = 0; s < F::SPC; ++s) {
+        const int64_t sig = g * F::SPC + s;
+        if (sig >= count) break;
+        const int64_t base = desc_step ? desc[sig].offset : sig * (int64_t)S::N;
+        xasync::bulk_g2s(stage + s * S::N, in + base, S::N * (uint32_t)sizeof(cpx<float>), bar);
+    }
+}
+
+// 3 CTAs fit per SM by shared memory (about 67 KB each) up to N = 4096.
+// TWC: compute twiddles instead of reading the table (with ~200 KB of shared
+// memory per SM the L1 left over may not hold the table).
+template <int L, bool TWC>
+__global__ void __launch_bounds__(fused_shape<L>::THREADS, (L <= 12 ? 3 : 1))
+k_xft_fused_tma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
+                const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+                const cpx<float>* __restrict__ tw, int32_t* __restrict__ status) {
+    using S = shape<L>;
+    using F = fused_shape<L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* stage = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* work = stage + F::SPC * S::N;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(work + F::SPC * S::NP);
+    const int64_t groups = (count + F::SPC - 1) / F::SPC;
+    int64_t g = blockIdx.x;
+    if (g >= groups) return;
+    const int tid = threadIdx.x;
+    const int sl = tid / S::T;
+    const int i = tid - sl * S::T;
+    cpx<float>* buf = work + sl * S::NP;
+    if (tid == 0) {
+        xasync::mbar_init(bar, 1);
+        xasync::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) issue_group<L>(in, desc, desc_step, count, g, stage, bar);
+    uint32_t parity = 0;
+    for (; g < groups; g += gridDim.x) {
+        bool ok = true;
+        if (tid == 0) ok = xasync::mbar_wait(bar, parity, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
+                xasync::mbar_wait(bar, parity, kWaitLimitNs);   // let the copy in flight land
+            }
+            return;
+        }
+        parity ^= 1u;
+        const int64_t sig = g * F::SPC + sl;
+        const bool active = sig < count;
+        const lct_desc D = desc[desc_step && active ? sig : 0];
+        const int64_t base = desc_step ? D.offset : sig * (int64_t)S::N;
+        const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+        cpx<float> v[S::E];
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int n = i + e * S::T;
+            cpx<float> f = {0.f, 0.f};
+            if (active) f = stage[sl * S::N + n];
+            v[e] = cmul(f, pre_w<L, float>(D, n, decay));
+        }
+        __syncthreads();                       // stage fully read
+        if (tid == 0 && g + gridDim.x < groups) {
+            xasync::fence_proxy_async_smem();
+            issue_group<L>(in, desc, desc_step, count, g + gridDim.x, stage, bar);
+        }
+        dft_signal<L, -1, TWC>(v, buf, i, tw);
+        if (active) {
+            const float sc = (float)D.scale;
+#pragma unroll
+            for (int e = 0; e < S::E; ++e) {
+                const int n = i + e * S::T;
+                out[base + n] = cscale(cmul(v[e], post_w<L, float>(D, n)), sc);
+            }
+        }
+    }
+}
+
+template <int L, bool TWC>
+cudaError_t launch_tma(const void* in, void* out, const lct_desc* desc, int desc_step,
+                       int64_t count, const void* tw, int32_t* status, cudaStream_t stream) {
+    using S = shape<L>;
+    using F = fused_shape<L>;
+    const size_t smem = (size_t)F::SPC * (S::N + S::NP) * sizeof(cpx<float>) + 16;
+    auto kern = k_xft_fused_tma<L, TWC>;
+    static int blocks_per_sm[64] = {};
+    static int sms[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!blocks_per_sm[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, F::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        blocks_per_sm[dev] = nb > 0 ? nb : 1;
+    }
+    const int64_t groups = (count + F::SPC - 1) / F::SPC;
+    int64_t grid = (int64_t)blocks_per_sm[dev] * sms[dev];
+    if (grid > groups) grid = groups;
+    kern<<<(unsigned)grid, F::THREADS, smem, stream>>>(
+        (const cpx<float>*)in, (cpx<float>*)out, desc, desc_step, count, (const cpx<float>*)tw, status);
+    return cudaGetLastError();
+}
+
 template <int L, class R>
 cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc_step,
-                       int64_t count, cudaStream_t stream) {
-    using S = xft_shape<L>;
-    const size_t smem = S::P > 1 ? (size_t)S::SPC * S::NP * sizeof(cpx<R>) : 0;
-    auto kern = k_xft_fused<L, R, true>;
+                       int64_t count, const void* tw, cudaStream_t stream) {
+    using S = shape<L>;
+    using F = fused_shape<L>;
+    const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
+    auto kern = k_xft_fused<L, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int64_t blocks = (count + S::SPC - 1) / S::SPC;
+    const int64_t blocks = (count + F::SPC - 1) / F::SPC;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, S::THREADS, smem, stream>>>(
-        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count);
+    kern<<<(unsigned)blocks, F::THREADS, smem, stream>>>(
+        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw);
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_dispatch(int log2n, const void* in, void* out, const lct_desc* desc,
-                            int desc_step, int64_t count, cudaStream_t stream) {
+                            int desc_step, int64_t count, const void* tw, cudaStream_t stream) {
     switch (log2n) {
 #define LCT_CASE(L) \
-    case L: return launch_one<L, R>(in, out, desc, desc_step, count, stream);
+    case L: return launch_one<L, R>(in, out, desc, desc_step, count, tw, stream);
         LCT_CASE(1) LCT_CASE(2) LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6)
         LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12)
+        LCT_CASE(13)
 #undef LCT_CASE
+        case 14:
+            if constexpr (sizeof(R) == 4) return launch_one<14, R>(in, out, desc, desc_step, count, tw, stream);
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
+bool lct_fused_tma_supported(int dtype, int log2n) {
+    return dtype == 0 && log2n >= 8 && log2n <= 13;
+}
+
+template <bool TWC>
+cudaError_t tma_dispatch(int log2n, const void* in, void* out, const lct_desc* desc,
+                         int desc_step, int64_t count, const void* tw, int32_t* status,
+                         cudaStream_t stream) {
+    switch (log2n) {
+        case 8: return launch_tma<8, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        case 9: return launch_tma<9, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        case 10: return launch_tma<10, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        case 11: return launch_tma<11, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        case 12: return launch_tma<12, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        case 13: return launch_tma<13, TWC>(in, out, desc, desc_step, count, tw, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t lct_launch_fused_tma(int dtype, int log2n, const void* in, void* out,
+                                 const lct_desc* desc, int desc_step, int64_t count,
+                                 const void* tw, int32_t* status, int twiddle_compute,
+                                 cudaStream_t stream) {
+    if (dtype != 0) return cudaErrorInvalidValue;
+    if (twiddle_compute)
+        return tma_dispatch<true>(log2n, in, out, desc, desc_step, count, tw, status, stream);
+    return tma_dispatch<false>(log2n, in, out, desc, desc_step, count, tw, status, stream);
+}
+
 bool lct_fused_supported(int dtype, int log2n) {
-    (void)dtype;
-    return log2n >= 1 && log2n <= 12;
+    return log2n >= 1 && log2n <= (dtype == 0 ? 14 : 13);
 }
 
 cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
-                             const lct_desc* desc, int desc_step, int64_t count,
+                             const lct_desc* desc, int desc_step, int64_t count, const void* tw,
                              cudaStream_t stream) {
-    if (dtype == 0) return launch_dispatch<float>(log2n, in, out, desc, desc_step, count, stream);
-    return launch_dispatch<double>(log2n, in, out, desc, desc_step, count, stream);
+    if (dtype == 0)
+        return launch_dispatch<float>(log2n, in, out, desc, desc_step, count, tw, stream);
+    return launch_dispatch<double>(log2n, in, out, desc, desc_step, count, tw, stream);
 }

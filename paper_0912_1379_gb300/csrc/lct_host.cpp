@@ -17,9 +17,14 @@
 
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <string>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 namespace {
@@ -184,6 +189,62 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// twiddle tables of the Stockham engine (xft_engine.cuh)
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tw_mu;
+std::map<std::tuple<int, int, int>, void*> g_tw;   // (device, dtype, log2n) -> table
+
+template <class T>
+std::vector<T> build_twiddles(int log2n) {
+    const int P = log2n >= 4 ? (log2n + 3) / 4 : 1;
+    const int R0 = 1 << (log2n - 4 * (P - 1));
+    std::vector<T> t;
+    for (int p = 1; p < P; ++p) {
+        const int64_t ns = (int64_t)R0 << (4 * (p - 1));
+        const int64_t M = 16 * ns;
+        for (int j = 1; j < 16; ++j)
+            for (int64_t k = 0; k < ns; ++k) {
+                const double ang = 2.0 * M_PI * (double)((j * k) % M) / (double)M;
+                t.push_back((T)std::cos(ang));
+                t.push_back((T)-std::sin(ang));
+            }
+    }
+    return t;
+}
+}  // namespace
+
+const void* lct_twiddle_table(int dtype, int log2n) {
+    if (log2n < 5) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    auto key = std::make_tuple(dev, dtype, log2n);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    void* d = nullptr;
+    size_t bytes;
+    cudaError_t e;
+    if (dtype == LCT_C64) {
+        std::vector<float> t = build_twiddles<float>(log2n);
+        bytes = t.size() * sizeof(float);
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+        e = cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<double> t = build_twiddles<double>(log2n);
+        bytes = t.size() * sizeof(double);
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+        e = cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    g_tw[key] = d;
+    return d;
+}
+
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {
     return (int)make_desc(N, p, offset, D);
 }
@@ -210,7 +271,72 @@ struct lct_plan_s {
     cufftHandle fft = 0;
     bool fft_valid = false;
     int64_t fft_n = 0, fft_batch = 0;
+    int variant = -1;               // -1: not chosen (cache or default 0)
 };
+
+// ---------------------------------------------------------------------------
+// autotune cache: (gpu name, dtype, log2n) -> variant
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string gpu_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return "unknown";
+    std::string n = prop.name;
+    for (char& ch : n)
+        if (ch == '|' || ch == '\n') ch = '_';
+    return n;
+}
+
+std::string tune_key(const std::string& gpu, int dtype, int log2n) {
+    return gpu + "|" + std::to_string(dtype) + "|" + std::to_string(log2n);
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("LCT_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        std::string s(line);
+        size_t p3 = s.rfind('|');
+        if (p3 == std::string::npos) continue;
+        int v = std::atoi(s.c_str() + p3 + 1);
+        g_tune[s.substr(0, p3)] = v;
+    }
+    std::fclose(f);
+}
+
+int tune_lookup(int dtype, int log2n) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(tune_key(gpu_name(), dtype, log2n));
+    return it == g_tune.end() ? -1 : it->second;
+}
+
+void tune_store(int dtype, int log2n, int variant) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load_locked();
+    std::string key = tune_key(gpu_name(), dtype, log2n);
+    g_tune[key] = variant;
+    const char* path = std::getenv("LCT_AUTOTUNE_CACHE");
+    if (path && *path) {
+        FILE* f = std::fopen(path, "a");
+        if (f) {
+            std::fprintf(f, "%s|%d\n", key.c_str(), variant);
+            std::fclose(f);
+        }
+    }
+}
+}  // namespace
 
 namespace {
 
@@ -329,6 +455,35 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
                                            count, stream));
 }
 
+// Can variant 1 (persistent, bulk-async prefetch) run this plan on `in`?
+bool tma_ok(lct_plan p, const void* in) {
+    if (!lct_fused_tma_supported(p->dtype, p->desc[0].log2n)) return false;
+    if (((uintptr_t)in) % 16) return false;
+    if (p->is_batch)
+        for (const lct_desc& D : p->desc)
+            if (D.offset % 2) return false;
+    return true;
+}
+
+int effective_variant(lct_plan p) {
+    if (p->variant >= 0) return p->variant;
+    int v = tune_lookup(p->dtype, p->desc[0].log2n);
+    return v >= 0 ? v : 0;
+}
+
+lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int desc_step,
+                     int variant, cudaStream_t stream) {
+    const int log2n = p->desc[0].log2n;
+    if (!lct_fused_supported(p->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
+    const void* tw = lct_twiddle_table(p->dtype, log2n);
+    if (log2n >= 5 && !tw) return LCT_ERR_OOM;
+    if ((variant == 1 || variant == 2) && tma_ok(p, in))
+        return from_cuda(lct_launch_fused_tma(p->dtype, log2n, in, out, p->d_desc, desc_step,
+                                              batch, tw, p->d_status, variant == 2, stream));
+    return from_cuda(lct_launch_fused(p->dtype, log2n, in, out, p->d_desc, desc_step, batch, tw,
+                                      stream));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -371,6 +526,68 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
     }
 }
 
+lct_status lct_plan_set_variant(lct_plan plan, int variant) {
+    if (!plan || variant < 0 || variant > 2) return LCT_ERR_ARG;
+    plan->variant = variant;
+    return LCT_OK;
+}
+
+lct_status lct_plan_get_variant(lct_plan plan, int* variant) {
+    if (!plan || !variant) return LCT_ERR_ARG;
+    *variant = plan->variant >= 0 ? plan->variant : 0;
+    return LCT_OK;
+}
+
+lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t batch,
+                             lct_stream_t stream_) {
+    if (!plan) return LCT_ERR_ARG;
+    if (plan->prec != LCT_PREC_NATIVE || plan->N0 == 0 || plan->desc[0].kind != LCT_KIND_XFT) {
+        plan->variant = 0;
+        return LCT_OK;
+    }
+    const int saved = plan->variant;
+    int candidates[3] = {0, 1, 2};
+    int n_cand = 1;
+    if (tma_ok(plan, in)) n_cand = 3;
+    if (n_cand == 1) {
+        plan->variant = 0;
+        return LCT_OK;
+    }
+    cudaStream_t stream = (cudaStream_t)stream_;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LCT_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LCT_ERR_CUDA;
+    }
+    float best_ms = 1e30f;
+    int best = 0;
+    lct_status st = LCT_OK;
+    for (int c = 0; c < n_cand && st == LCT_OK; ++c) {
+        plan->variant = candidates[c];
+        for (int w = 0; w < 2 && st == LCT_OK; ++w) st = lct_execute(plan, in, out, batch, stream_);
+        if (st != LCT_OK) break;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 5 && st == LCT_OK; ++r) st = lct_execute(plan, in, out, batch, stream_);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = LCT_ERR_CUDA;
+        float ms = 0.f;
+        if (st == LCT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = candidates[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LCT_OK) {
+        plan->variant = saved;
+        return st;
+    }
+    plan->variant = best;
+    tune_store(plan->dtype, plan->desc[0].log2n, best);
+    return LCT_OK;
+}
+
 lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                        lct_stream_t stream_) {
     if (!plan) return LCT_ERR_ARG;
@@ -404,9 +621,7 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
         }
         return run_plain(plan, in, out, batch, desc_step, stream);
     }
-    if (!lct_fused_supported(plan->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
-    return from_cuda(lct_launch_fused(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
-                                      batch, stream));
+    return run_fused(plan, in, out, batch, desc_step, effective_variant(plan), stream);
 }
 
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,

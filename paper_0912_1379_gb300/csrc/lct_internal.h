@@ -48,15 +48,33 @@ enum { LCT_DEV_OK = 0, LCT_DEV_BAD_DESC = 1, LCT_DEV_TIMEOUT = 2 };
 // lct_plan_create; returns an lct_status value).
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D);
 
+// Host: device twiddle table of the Stockham engine for N = 2^log2n on the
+// current device (built once per device, dtype and N; owned by the library
+// for the life of the process).  Layout [pass p = 1..P-1][j = 1..15][k < Ns_p]:
+// entry e^{-2 pi i j k / (16 Ns_p)}, Ns_p = R0 16^(p-1), R0 the first radix.
+// Returns nullptr on failure (and for N < 32, which needs no table).
+const void* lct_twiddle_table(int dtype, int log2n);
+
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 // Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
 // desc_step = 0: one descriptor for all `count` signals (signal s at s*N);
 // desc_step = 1: desc[s] for signal s (its own offset).
 // dtype: 0 = complex64 (FP32 arithmetic), 1 = complex128 (FP64 arithmetic).
+// tw: the twiddle table of lct_twiddle_table(dtype, log2n).
 cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
-                             const lct_desc* desc, int desc_step, int64_t count,
+                             const lct_desc* desc, int desc_step, int64_t count, const void* tw,
                              cudaStream_t stream);
 bool lct_fused_supported(int dtype, int log2n);
+
+// Persistent variant of the fused kernel with bulk-async prefetch of the next
+// signal group (complex64, N = 256 .. 8192).  Signal starts must be 16-byte
+// aligned.  status: device status word (a timed-out wait records LCT_DEV_TIMEOUT).
+// twiddle_compute: 1 = compute twiddles in registers, 0 = read the table.
+cudaError_t lct_launch_fused_tma(int dtype, int log2n, const void* in, void* out,
+                                 const lct_desc* desc, int desc_step, int64_t count,
+                                 const void* tw, int32_t* status, int twiddle_compute,
+                                 cudaStream_t stream);
+bool lct_fused_tma_supported(int dtype, int log2n);
 
 // Diagonal branch (b == 0) for `count` signals of N = 2^log2n.
 cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,

@@ -1,0 +1,170 @@
+// Stockham DFT engine shared by the XFT kernels.
+//
+// Self-sorting Stockham formulation of the N-point DFT (N = 2^L).  Every
+// thread owns E = 16 samples (E = N for N < 16), T = N/E threads per signal.
+// Pass p has radix R_p (first pass 2^(L mod 4) or 16, then 16) and
+// sub-length Ns_p = product of the previous radices.  In every pass thread i
+// holds the samples i + e T (e = 0..E-1) -- the coalesced pattern, so the
+// first pass can read global memory directly and the last pass can write it
+// directly -- multiplies sample j of its group by the twiddle
+// e^{S 2 pi i j k / (Ns R)} (k = i' mod Ns), applies a radix-R DFT in
+// registers, and writes sample j of virtual thread i' to position
+// (i' - k) R + k + j Ns of the next pass's buffer.  Shared memory is padded
+// by one slot per 16 samples, which makes every exchange free of bank
+// conflicts (for T >= 16).
+//
+// Twiddles come from a per-N table laid out [pass][j-1][k] (see
+// lct_twiddle_table), so that the 32 lanes of a warp read 32 consecutive
+// entries.  Entry (p, j, k) = e^{-2 pi i j k / (16 Ns_p)}; the inverse
+// transform (S = +1) uses the conjugate.
+#pragma once
+#include "xft_common.cuh"
+
+namespace xft {
+
+constexpr int pass_count(int L) { return L >= 4 ? (L + 3) / 4 : 1; }
+constexpr int first_radix(int L) { return 1 << (L - 4 * (pass_count(L) - 1)); }
+__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+
+template <int L>
+struct shape {
+    static constexpr int N = 1 << L;
+    static constexpr int E = L >= 4 ? 16 : N;
+    static constexpr int T = N / E;
+    static constexpr int P = pass_count(L);
+    static constexpr int NP = N + (N >> 4);
+};
+
+template <int L, int p>
+struct pass {
+    static constexpr int RADIX = p == 0 ? first_radix(L) : 16;
+    static constexpr int NS = p == 0 ? 1 : first_radix(L) << (4 * (p - 1));
+    static constexpr int TW_OFF = NS - first_radix(L);   // sum of (16-1) Ns_q over q < p
+};
+
+template <class R>
+__device__ __forceinline__ cpx<R> ld_tw(const cpx<R>* p);
+template <>
+__device__ __forceinline__ cpx<float> ld_tw<float>(const cpx<float>* p) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+template <>
+__device__ __forceinline__ cpx<double> ld_tw<double>(const cpx<double>* p) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
+
+// e^{SGN 2 pi i k / M} (M a power of two, so 2k/M is exact), correctly
+// rounded library sincospi.
+template <class R, int SGN>
+__device__ __forceinline__ cpx<R> twiddle_exact(int k, int M) {
+    R s, c;
+    if constexpr (sizeof(R) == 4) sincospif((float)(2 * k) / (float)M, &s, &c);
+    else sincospi((double)(2 * k) / (double)M, &s, &c);
+    return {c, SGN < 0 ? -s : s};
+}
+
+// Twiddles + radix-R DFTs of pass p on the registers of thread i.
+// TWC = false: twiddles read from the table; TWC = true: computed (one
+// sincospi for w = e^{S 2 pi i k/(Ns R)}, then powers by a product tree).
+template <int L, int p, int SGN, bool TWC, class R>
+__device__ __forceinline__ void butterflies(cpx<R>* v, int i, const cpx<R>* __restrict__ tw) {
+    using S = shape<L>;
+    using PI = pass<L, p>;
+    constexpr int RADIX = PI::RADIX, NS = PI::NS, V = S::E / RADIX;
+#pragma unroll
+    for (int vv = 0; vv < V; ++vv) {
+        cpx<R> u[RADIX];
+#pragma unroll
+        for (int j = 0; j < RADIX; ++j) u[j] = v[vv + j * V];
+        if (NS > 1) {
+            const int k = (i + vv * S::T) & (NS - 1);
+            if constexpr (TWC) {
+                cpx<R> w[RADIX];
+                twiddle_powers<RADIX>(twiddle_exact<R, SGN>(k, NS * RADIX), w);
+#pragma unroll
+                for (int j = 1; j < RADIX; ++j) u[j] = cmul(u[j], w[j]);
+            } else {
+                const cpx<R>* t = tw + PI::TW_OFF + k;
+#pragma unroll
+                for (int j = 1; j < RADIX; ++j) {
+                    cpx<R> w = ld_tw<R>(t + (j - 1) * NS);
+                    if (SGN > 0) w.y = -w.y;
+                    u[j] = cmul(u[j], w);
+                }
+            }
+        }
+        dft<RADIX, SGN>(u);
+#pragma unroll
+        for (int j = 0; j < RADIX; ++j) v[vv + j * V] = u[j];
+    }
+}
+
+template <int L, int p, class R>
+__device__ __forceinline__ void smem_store(const cpx<R>* v, cpx<R>* buf, int i) {
+    using S = shape<L>;
+    using PI = pass<L, p>;
+    constexpr int RADIX = PI::RADIX, NS = PI::NS, V = S::E / RADIX;
+#pragma unroll
+    for (int vv = 0; vv < V; ++vv) {
+        const int ip = i + vv * S::T;
+        const int k = ip & (NS - 1);
+        const int base = (ip - k) * RADIX + k;
+#pragma unroll
+        for (int j = 0; j < RADIX; ++j) buf[pad_idx(base + j * NS)] = v[vv + j * V];
+    }
+}
+
+template <int L, class R>
+__device__ __forceinline__ void smem_load(cpx<R>* v, const cpx<R>* buf, int i) {
+    using S = shape<L>;
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) v[e] = buf[pad_idx(i + e * S::T)];
+}
+
+// Passes p..P-1, the first of which reads the shared-memory output of pass p-1.
+template <int L, int p, int SGN, bool TWC, class R>
+struct passes_from {
+    __device__ __forceinline__ static void run(cpx<R>* v, cpx<R>* buf, int i,
+                                               const cpx<R>* __restrict__ tw) {
+        if (p > 1) __syncthreads();          // previous exchange fully read
+        smem_store<L, p - 1>(v, buf, i);
+        __syncthreads();
+        smem_load<L>(v, buf, i);
+        butterflies<L, p, SGN, TWC>(v, i, tw);
+        passes_from<L, p + 1, SGN, TWC, R>::run(v, buf, i, tw);
+    }
+};
+template <int L, int SGN, bool TWC, class R>
+struct passes_from<L, shape<L>::P, SGN, TWC, R> {
+    __device__ __forceinline__ static void run(cpx<R>*, cpx<R>*, int, const cpx<R>* __restrict__) {}
+};
+
+// Whole DFT on the registers v (thread i holds samples i + e T on entry and
+// output samples i + e T on exit).  buf: this signal's padded shared buffer.
+template <int L, int SGN, bool TWC = false, class R>
+__device__ __forceinline__ void dft_signal(cpx<R>* v, cpx<R>* buf, int i,
+                                           const cpx<R>* __restrict__ tw) {
+    butterflies<L, 0, SGN, TWC>(v, i, tw);
+    passes_from<L, 1, SGN, TWC, R>::run(v, buf, i, tw);
+}
+
+// Streaming global load that does not allocate in L1 (keeps the twiddle
+// table resident): ld.global.nc.L1::no_allocate.
+__device__ __forceinline__ cpx<float> ld_stream(const cpx<float>* p) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ld_stream(const cpx<double>* p) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "l"(p));
+    return {v.x, v.y};
+}
+
+}  // namespace xft

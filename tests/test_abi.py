@@ -91,6 +91,19 @@ def test_execute_validation_without_gpu():
         lct.lct_plan_destroy(bp)
 
 
+def test_variant_selection_host_only():
+    p = lct.lct_plan_create(1024, 1.0, 2.0, 0.5, 2.0)
+    try:
+        assert lct.lct_plan_get_variant(p) == 0
+        lct.lct_plan_set_variant(p, 1)
+        assert lct.lct_plan_get_variant(p) == 1
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_plan_set_variant(p, 7)
+        assert e.value.status == 1
+    finally:
+        lct.lct_plan_destroy(p)
+
+
 @pytest.mark.parametrize("z", [0.0, 1.5, 2j, complex(float("nan"), 0)])
 def test_frft_bad_z(z):
     with pytest.raises(lct.LctError) as e:

@@ -68,9 +68,11 @@ def test_config0_fp64(prec):
 # --------------------------------------------------------------------------
 # every supported N, both precisions, ragged batch counts
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("log2n", list(range(1, 13)))
+@pytest.mark.parametrize("log2n", list(range(1, 15)))
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
 def test_every_size(log2n, dtype):
+    if dtype == np.complex128 and log2n > 13:
+        pytest.skip("complex128 fused path stops at N = 8192")
     N = 1 << log2n
     count = 37 if N <= 1024 else 5           # not a multiple of the signals per CTA
     x = O.nodes(N)
@@ -102,6 +104,40 @@ def test_uniform_batch_per_signal_params(N, count, seed):
     ref = O.lct(f.astype(np.complex128), params)
     err = rel_l2(G, ref)
     assert err.max() < TOL32
+
+
+@pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30)])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_kernel_variants(N, count, variant):
+    """Both fused variants (one CTA per group / persistent with bulk-async
+    prefetch) on per-signal parameters, with a ragged last group."""
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=N + variant, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N).set_variant(variant)
+    try:
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    idx = np.unique(np.linspace(0, count - 1, 24).astype(int))
+    ref = O.lct(f[idx].astype(np.complex128), params[idx])
+    assert rel_l2(G[idx], ref).max() < TOL32
+
+
+def test_autotune_picks_a_valid_variant():
+    N, count = 4096, 512
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=21, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N)
+    try:
+        xin = to_dev(f, np.complex64)
+        out = torch.empty_like(xin)
+        v = p.autotune(xin, out, count)
+        assert v in (0, 1, 2)
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    ref = O.lct(f[:8].astype(np.complex128), params[:8])
+    assert rel_l2(G[:8], ref).max() < TOL32
 
 
 def test_in_place_equals_out_of_place():
