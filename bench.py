@@ -40,7 +40,9 @@ METRIC = "LCT points/s at N=4096 batched vs plain FP64 GPU path at <=1e-5 rel er
 N_DEFAULT, COUNT_DEFAULT = 4096, 16384
 BYTES_PER_POINT = 16          # complex64: 8 B read + 8 B written
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/xft_common.cuh"]
+KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/k_fused_pair.cu",
+                  "paper_0912_1379_gb300/csrc/xft_common.cuh", "paper_0912_1379_gb300/csrc/xft_engine.cuh",
+                  "paper_0912_1379_gb300/csrc/xft_chirp.cuh", "paper_0912_1379_gb300/csrc/xft_async.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_xft_fused_f32_n4096.json")
 
 
@@ -56,7 +58,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4"],
                     help="fused kernel variant (auto: the library's autotuner)")
     return ap.parse_args()
 
@@ -313,7 +315,7 @@ def main():
     achieved = n_points * BYTES_PER_POINT / (ms_per_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_per_launch(n_points),
-                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>"}[variant]
+                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>"}[variant]
                           + " (N=4096, complex64)",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}

@@ -114,7 +114,12 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     bulk asynchronous copies while the current one is transformed
  *     (complex64, N = 256 .. 8192, 16-byte aligned signal starts; other
  *     plans fall back to variant 0), twiddles read from the table;
- *  2  as 1 with twiddles computed in registers.
+ *  2  as 1 with twiddles computed in registers;
+ *  3  paired: every thread carries two signals in packed f32x2 registers,
+ *     halving the arithmetic instructions (complex64, N = 32 .. 8192);
+ *  4  paired and persistent, the next pair brought in by bulk asynchronous
+ *     copy while the current one is written out (complex64, N = 4096,
+ *     16-byte aligned signal starts; else variant 3).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 lct_status lct_plan_get_variant(lct_plan plan, int* variant);

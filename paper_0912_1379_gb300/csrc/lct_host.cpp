@@ -245,6 +245,33 @@ const void* lct_twiddle_table(int dtype, int log2n) {
     return d;
 }
 
+const void* lct_twiddle_table_pair(int log2n) {
+    if (log2n < 5) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    auto key = std::make_tuple(dev, 2, log2n);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    std::vector<float> t = build_twiddles<float>(log2n);
+    std::vector<float> b(2 * t.size());
+    for (size_t k = 0; k < t.size() / 2; ++k) {
+        b[4 * k + 0] = t[2 * k];
+        b[4 * k + 1] = t[2 * k];
+        b[4 * k + 2] = t[2 * k + 1];
+        b[4 * k + 3] = t[2 * k + 1];
+    }
+    void* d = nullptr;
+    const size_t bytes = b.size() * sizeof(float);
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, b.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    g_tw[key] = d;
+    return d;
+}
+
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {
     return (int)make_desc(N, p, offset, D);
 }
@@ -455,6 +482,19 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
                                            count, stream));
 }
 
+// Can a bulk-async variant run this plan on `in` (16-byte aligned starts)?
+bool tma_aligned(lct_plan p, const void* in) {
+    if (((uintptr_t)in) % 16) return false;
+    if (p->is_batch)
+        for (const lct_desc& D : p->desc)
+            if (D.offset % 2) return false;
+    return true;
+}
+
+bool pair_tma_ok(lct_plan p, const void* in) {
+    return lct_fused_pair_tma_supported(p->dtype, p->desc[0].log2n) && tma_aligned(p, in);
+}
+
 // Can variant 1 (persistent, bulk-async prefetch) run this plan on `in`?
 bool tma_ok(lct_plan p, const void* in) {
     if (!lct_fused_tma_supported(p->dtype, p->desc[0].log2n)) return false;
@@ -477,6 +517,18 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
     if (!lct_fused_supported(p->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
     const void* tw = lct_twiddle_table(p->dtype, log2n);
     if (log2n >= 5 && !tw) return LCT_ERR_OOM;
+    if (variant == 4 && pair_tma_ok(p, in)) {
+        const void* tw2 = lct_twiddle_table_pair(log2n);
+        if (!tw2) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_fused_pair_tma(p->dtype, log2n, in, out, p->d_desc,
+                                                   desc_step, batch, tw2, p->d_status, stream));
+    }
+    if ((variant == 3 || variant == 4) && lct_fused_pair_supported(p->dtype, log2n)) {
+        const void* tw2 = lct_twiddle_table_pair(log2n);
+        if (!tw2) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_fused_pair(p->dtype, log2n, in, out, p->d_desc, desc_step,
+                                               batch, tw2, stream));
+    }
     if ((variant == 1 || variant == 2) && tma_ok(p, in))
         return from_cuda(lct_launch_fused_tma(p->dtype, log2n, in, out, p->d_desc, desc_step,
                                               batch, tw, p->d_status, variant == 2, stream));
@@ -527,7 +579,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 2) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 4) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }
@@ -546,9 +598,14 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         return LCT_OK;
     }
     const int saved = plan->variant;
-    int candidates[3] = {0, 1, 2};
+    int candidates[5] = {0, 0, 0, 0, 0};
     int n_cand = 1;
-    if (tma_ok(plan, in)) n_cand = 3;
+    if (lct_fused_pair_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 3;
+    if (pair_tma_ok(plan, in)) candidates[n_cand++] = 4;
+    if (tma_ok(plan, in)) {
+        candidates[n_cand++] = 1;
+        candidates[n_cand++] = 2;
+    }
     if (n_cand == 1) {
         plan->variant = 0;
         return LCT_OK;

@@ -54,6 +54,9 @@ int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D);
 // entry e^{-2 pi i j k / (16 Ns_p)}, Ns_p = R0 16^(p-1), R0 the first radix.
 // Returns nullptr on failure (and for N < 32, which needs no table).
 const void* lct_twiddle_table(int dtype, int log2n);
+// Broadcast form of the complex64 table for the paired kernel: every entry
+// (wx, wy) stored as {(wx, wx), (wy, wy)} (16 bytes).
+const void* lct_twiddle_table_pair(int log2n);
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 // Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
@@ -75,6 +78,20 @@ cudaError_t lct_launch_fused_tma(int dtype, int log2n, const void* in, void* out
                                  const void* tw, int32_t* status, int twiddle_compute,
                                  cudaStream_t stream);
 bool lct_fused_tma_supported(int dtype, int log2n);
+
+// Paired variant (complex64, N = 32 .. 8192): two signals per thread in
+// packed f32x2 registers.  tw_pair: lct_twiddle_table_pair(log2n).
+cudaError_t lct_launch_fused_pair(int dtype, int log2n, const void* in, void* out,
+                                  const lct_desc* desc, int desc_step, int64_t count,
+                                  const void* tw_pair, cudaStream_t stream);
+bool lct_fused_pair_supported(int dtype, int log2n);
+
+// Persistent paired variant with bulk-async refill of its single shared
+// buffer (complex64, N = 4096, 16-byte aligned signal starts).
+cudaError_t lct_launch_fused_pair_tma(int dtype, int log2n, const void* in, void* out,
+                                      const lct_desc* desc, int desc_step, int64_t count,
+                                      const void* tw_pair, int32_t* status, cudaStream_t stream);
+bool lct_fused_pair_tma_supported(int dtype, int log2n);
 
 // Diagonal branch (b == 0) for `count` signals of N = 2^log2n.
 cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,

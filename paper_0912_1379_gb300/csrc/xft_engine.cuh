@@ -54,6 +54,12 @@ __device__ __forceinline__ cpx<double> ld_tw<double>(const cpx<double>* p) {
     double2 v = __ldg(reinterpret_cast<const double2*>(p));
     return {v.x, v.y};
 }
+// broadcast-form entry {(wx, wx), (wy, wy)} for packed pairs
+template <>
+__device__ __forceinline__ cpx<pf> ld_tw<pf>(const cpx<pf>* p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {pf{make_float2(v.x, v.y)}, pf{make_float2(v.z, v.w)}};
+}
 
 // e^{SGN 2 pi i k / M} (M a power of two, so 2k/M is exact), correctly
 // rounded library sincospi.
