@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
                     help="fused kernel variant (auto: the library's autotuner)")
     return ap.parse_args()
 

@@ -119,7 +119,10 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     halving the arithmetic instructions (complex64, N = 32 .. 8192);
  *  4  paired and persistent, the next pair brought in by bulk asynchronous
  *     copy while the current one is written out (complex64, N = 4096,
- *     16-byte aligned signal starts; else variant 3).
+ *     16-byte aligned signal starts; else variant 3);
+ *  5  thread-block cluster of N/8192 CTAs per signal exchanging through
+ *     distributed shared memory (N = 16384 .. 65536; the only kernel for
+ *     N >= 32768 in complex64 and N >= 16384 in complex128).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 lct_status lct_plan_get_variant(lct_plan plan, int* variant);

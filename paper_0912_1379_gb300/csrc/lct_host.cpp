@@ -514,6 +514,13 @@ int effective_variant(lct_plan p) {
 lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int desc_step,
                      int variant, cudaStream_t stream) {
     const int log2n = p->desc[0].log2n;
+    const int lm = lct_cluster_local_log2(p->dtype, log2n);
+    if (lm >= 0 && (variant == 5 || !lct_fused_supported(p->dtype, log2n))) {
+        const void* twl = lct_twiddle_table(p->dtype, lm);
+        if (!twl) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_cluster(p->dtype, log2n, in, out, p->d_desc, desc_step, batch,
+                                            twl, stream));
+    }
     if (!lct_fused_supported(p->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
     const void* tw = lct_twiddle_table(p->dtype, log2n);
     if (log2n >= 5 && !tw) return LCT_ERR_OOM;
@@ -579,7 +586,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 4) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 5) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }
@@ -598,8 +605,11 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         return LCT_OK;
     }
     const int saved = plan->variant;
-    int candidates[5] = {0, 0, 0, 0, 0};
+    int candidates[6] = {0, 0, 0, 0, 0, 0};
     int n_cand = 1;
+    if (lct_cluster_local_log2(plan->dtype, plan->desc[0].log2n) >= 0 &&
+        lct_fused_supported(plan->dtype, plan->desc[0].log2n))
+        candidates[n_cand++] = 5;
     if (lct_fused_pair_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 3;
     if (pair_tma_ok(plan, in)) candidates[n_cand++] = 4;
     if (tma_ok(plan, in)) {

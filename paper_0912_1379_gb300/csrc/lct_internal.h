@@ -69,6 +69,14 @@ cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
                              cudaStream_t stream);
 bool lct_fused_supported(int dtype, int log2n);
 
+// Large-N fused kernel (N = 16384 .. 65536, both dtypes): a thread-block
+// cluster of N/8192 CTAs per signal exchanging through distributed shared
+// memory.  tw_local: lct_twiddle_table(dtype, lct_cluster_local_log2(...)).
+int lct_cluster_local_log2(int dtype, int log2n);     // -1 if unsupported
+cudaError_t lct_launch_cluster(int dtype, int log2n, const void* in, void* out,
+                               const lct_desc* desc, int desc_step, int64_t count,
+                               const void* tw_local, cudaStream_t stream);
+
 // Persistent variant of the fused kernel with bulk-async prefetch of the next
 // signal group (complex64, N = 256 .. 8192).  Signal starts must be 16-byte
 // aligned.  status: device status word (a timed-out wait records LCT_DEV_TIMEOUT).

@@ -68,13 +68,11 @@ def test_config0_fp64(prec):
 # --------------------------------------------------------------------------
 # every supported N, both precisions, ragged batch counts
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("log2n", list(range(1, 15)))
+@pytest.mark.parametrize("log2n", list(range(1, 17)))
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
 def test_every_size(log2n, dtype):
-    if dtype == np.complex128 and log2n > 13:
-        pytest.skip("complex128 fused path stops at N = 8192")
     N = 1 << log2n
-    count = 37 if N <= 1024 else 5           # not a multiple of the signals per CTA
+    count = 37 if N <= 1024 else (5 if N <= 16384 else 2)   # ragged w.r.t. signals per CTA
     x = O.nodes(N)
     params, f = W.uniform_batch(x, count, seed=100 + log2n, dtype=np.complex128)
     abcd = (0.37, -1.3, (0.37 * 0.8 - 1) / -1.3, 0.8)
@@ -106,8 +104,8 @@ def test_uniform_batch_per_signal_params(N, count, seed):
     assert err.max() < TOL32
 
 
-@pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30), (16384, 9)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_kernel_variants(N, count, variant):
     """Both fused variants (one CTA per group / persistent with bulk-async
     prefetch) on per-signal parameters, with a ragged last group."""
@@ -118,7 +116,8 @@ def test_kernel_variants(N, count, variant):
         G = run(p.handle, f, np.complex64)
     finally:
         p.destroy()
-    idx = np.unique(np.linspace(0, count - 1, 24).astype(int))
+    n_check = 24 if N <= 4096 else 3                  # oracle cost grows as N^2
+    idx = np.unique(np.linspace(0, count - 1, n_check).astype(int))
     ref = O.lct(f[idx].astype(np.complex128), params[idx])
     assert rel_l2(G[idx], ref).max() < TOL32
 
@@ -132,7 +131,7 @@ def test_autotune_picks_a_valid_variant():
         xin = to_dev(f, np.complex64)
         out = torch.empty_like(xin)
         v = p.autotune(xin, out, count)
-        assert v in (0, 1, 2, 3, 4)
+        assert v in (0, 1, 2, 3, 4, 5)
         G = run(p.handle, f, np.complex64)
     finally:
         p.destroy()
