@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
     ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
                     help="fused kernel variant (auto: the library's autotuner)")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
+                    help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
+                         "instances in one graph launch")
     return ap.parse_args()
 
 
@@ -221,6 +224,64 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# ragged workload: 20000 instances, N = 2^6..2^16, four kinds, one graph launch
+# ---------------------------------------------------------------------------
+def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+    r = W.ragged_plan(seed=W.SEED_RAGGED + rank)
+    M = len(r["kind"])
+    Ns = (1 << r["log2n"]).astype(np.int64)
+    abcd = r["abcd"].copy()
+    for s in np.nonzero(r["kind"] == W.KIND_FRFT)[0]:
+        z = complex(r["z"][s])
+        abcd[s] = [(z + 1 / z) / 2, (1 / z - z) / 2j, 1j * (1 / z - z) / 2, (z + 1 / z) / 2]
+    offs = np.concatenate([[0], np.cumsum(Ns)[:-1]]).astype(np.int64)
+    total = int(Ns.sum())
+    buf = np.empty(total, dtype=np.complex64)
+    rng = r["rng"]
+    for s in range(M):
+        buf[offs[s]:offs[s] + Ns[s]] = W.ragged_signal(lct.lct_input_grid(int(Ns[s])), r["s"][s],
+                                                       r["q"][s], rng)
+    plan = lct.Plan.batch(Ns, abcd, offs, dtype=lct.LCT_C64)
+    d_in = torch.from_numpy(buf).cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.execute(d_in, d_out, M, stream)
+    torch.cuda.synchronize()
+    if lct.lct_device_status(plan.handle) != 0:
+        raise RuntimeError("device status after warm-up")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(d_in, d_out, M, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1)) / args.steps
+    plan.destroy()
+    value = world * total / (ms * 1e-3)
+    peak, peak_kind = measured_peak()
+    achieved = total * BYTES_PER_POINT / (ms * 1e-3) / 1e9
+    if rank == 0:
+        by_n = {int(n): int((Ns == n).sum()) for n in np.unique(Ns)}
+        print(json.dumps({
+            "metric": "LCT points/s, ragged batch (20000 instances, N=2^6..2^16, 4 kinds)",
+            "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ragged: 20000 instances (9000 generic, 5000 complex-z FrFT, "
+                                   "4000 Fourier, 2000 b=0), log2 N ~ U{6..16}, seed %d" % W.SEED_RAGGED,
+                       "points": total, "signals_by_N": by_n,
+                       "l2": "inputs larger than L2 (1.9 GB per buffer)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+            "gpu_launches": None,
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -251,6 +312,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.workload == "ragged":
+        return ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
     N, count = args.n, args.count
     x = lct.lct_input_grid(N)
     params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)

@@ -39,11 +39,17 @@ __device__ __forceinline__ cpx<R> post_n(const lct_desc& D, int n) {
 template <class R>
 __device__ __forceinline__ cpx<R> ld_in(const cpx<R>* p) { return ld_stream(p); }
 
+// Resident CTAs per SM: 4 x 256 threads (complex64, 4096-point rows),
+// 1 x 512 threads (complex128, 8192-point rows).
+template <int LM, class R>
+constexpr int cluster_min_blocks() { return sizeof(R) == 4 ? (LM <= 12 ? 4 : 2) : 1; }
+
 template <int LM, int LC, class R>
-__global__ void __launch_bounds__(shape<LM>::T, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(shape<LM>::T, (cluster_min_blocks<LM, R>()))
 k_xft_cluster(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
               const lct_desc* __restrict__ desc, int desc_step, int64_t count,
-              const cpx<R>* __restrict__ tw) {
+              const cpx<R>* __restrict__ tw, const int32_t* __restrict__ idx,
+              int32_t* __restrict__ status) {
     using S = shape<LM>;
     constexpr int C = 1 << LC, M = S::N, LN = LM + LC, N = 1 << LN;
     constexpr int Q = S::E / C;              // step-A positions per thread
@@ -54,8 +60,13 @@ k_xft_cluster(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     const int c = (int)cl.block_rank();
     const int64_t sig = blockIdx.x / C;
     const int i = threadIdx.x;
-    const bool active = sig < count;
-    const lct_desc D = desc[desc_step && active ? sig : 0];
+    bool active = sig < count;
+    const int64_t gsig = idx ? (active ? idx[sig] : 0) : sig;
+    const lct_desc D = desc[desc_step && active ? gsig : 0];
+    if (idx && active && (D.log2n != LN || D.kind != LCT_KIND_XFT || D.offset < 0)) {
+        if (i == 0 && c == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+        active = false;                       // uniform over the cluster: every CTA reads D
+    }
     const int64_t base = desc_step ? D.offset : sig * (int64_t)N;
     const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
 
@@ -119,7 +130,8 @@ k_xft_cluster(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
 
 template <int LM, int LC, class R>
 cudaError_t launch_cluster(const void* in, void* out, const lct_desc* desc, int desc_step,
-                           int64_t count, const void* tw, cudaStream_t stream) {
+                           int64_t count, const void* tw, const int32_t* idx, int32_t* status,
+                           cudaStream_t stream) {
     using S = shape<LM>;
     constexpr int C = 1 << LC;
     const size_t smem = (size_t)S::NP * sizeof(cpx<R>);
@@ -141,12 +153,14 @@ cudaError_t launch_cluster(const void* in, void* out, const lct_desc* desc, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count,
-                              (const cpx<R>*)tw);
+                              (const cpx<R>*)tw, idx, status);
 }
 
 }  // namespace
 
 // Local length M = 8192 for both precisions; C = N / 8192 CTAs per cluster.
+// (Measured on GB300: 4096-point rows with C = 8 / 16 were slower -- the
+// distributed shared-memory exchange, not the row transform, dominates.)
 int lct_cluster_local_log2(int dtype, int log2n) {
     (void)dtype;
     return (log2n >= 14 && log2n <= 16) ? 13 : -1;
@@ -154,19 +168,20 @@ int lct_cluster_local_log2(int dtype, int log2n) {
 
 cudaError_t lct_launch_cluster(int dtype, int log2n, const void* in, void* out,
                                const lct_desc* desc, int desc_step, int64_t count,
-                               const void* tw_local, cudaStream_t stream) {
+                               const void* tw_local, const int32_t* idx, int32_t* status,
+                               cudaStream_t stream) {
     if (dtype == 0) {
         switch (log2n) {
-            case 14: return launch_cluster<13, 1, float>(in, out, desc, desc_step, count, tw_local, stream);
-            case 15: return launch_cluster<13, 2, float>(in, out, desc, desc_step, count, tw_local, stream);
-            case 16: return launch_cluster<13, 3, float>(in, out, desc, desc_step, count, tw_local, stream);
+            case 14: return launch_cluster<13, 1, float>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
+            case 15: return launch_cluster<13, 2, float>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
+            case 16: return launch_cluster<13, 3, float>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (log2n) {
-        case 14: return launch_cluster<13, 1, double>(in, out, desc, desc_step, count, tw_local, stream);
-        case 15: return launch_cluster<13, 2, double>(in, out, desc, desc_step, count, tw_local, stream);
-        case 16: return launch_cluster<13, 3, double>(in, out, desc, desc_step, count, tw_local, stream);
+        case 14: return launch_cluster<13, 1, double>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
+        case 15: return launch_cluster<13, 2, double>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
+        case 16: return launch_cluster<13, 3, double>(in, out, desc, desc_step, count, tw_local, idx, status, stream);
         default: return cudaErrorInvalidValue;
     }
 }

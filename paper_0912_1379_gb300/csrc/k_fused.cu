@@ -32,7 +32,8 @@ template <int L, class R>
 __global__ void __launch_bounds__(fused_shape<L>::THREADS, (min_blocks<L, R>()))
 k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
             const lct_desc* __restrict__ desc, int desc_step, int64_t count,
-            const cpx<R>* __restrict__ tw) {
+            const cpx<R>* __restrict__ tw, const int32_t* __restrict__ idx,
+            int32_t* __restrict__ status) {
     using S = shape<L>;
     using F = fused_shape<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -41,8 +42,15 @@ k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     const int sl = tid / S::T;
     const int i = tid - sl * S::T;
     const int64_t sig = (int64_t)blockIdx.x * F::SPC + sl;
-    const bool active = sig < count;
-    const lct_desc D = desc[desc_step && active ? sig : 0];
+    bool active = sig < count;
+    // idx (ragged batches): this launch's signal s is descriptor idx[s]; a
+    // descriptor that does not match the kernel is flagged, not transformed.
+    const int64_t gsig = idx ? (active ? idx[sig] : 0) : sig;
+    const lct_desc D = desc[desc_step && active ? gsig : 0];
+    if (idx && active && (D.log2n != L || D.kind != LCT_KIND_XFT || D.offset < 0)) {
+        if (i == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+        active = false;
+    }
     const int64_t base = desc_step ? D.offset : sig * (int64_t)S::N;
     cpx<R>* buf = smem + sl * S::NP;
     const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
@@ -195,7 +203,8 @@ cudaError_t launch_tma(const void* in, void* out, const lct_desc* desc, int desc
 
 template <int L, class R>
 cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc_step,
-                       int64_t count, const void* tw, cudaStream_t stream) {
+                       int64_t count, const void* tw, const int32_t* idx, int32_t* status,
+                       cudaStream_t stream) {
     using S = shape<L>;
     using F = fused_shape<L>;
     const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
@@ -208,22 +217,24 @@ cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc
     const int64_t blocks = (count + F::SPC - 1) / F::SPC;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     kern<<<(unsigned)blocks, F::THREADS, smem, stream>>>(
-        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw);
+        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw, idx, status);
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_dispatch(int log2n, const void* in, void* out, const lct_desc* desc,
-                            int desc_step, int64_t count, const void* tw, cudaStream_t stream) {
+                            int desc_step, int64_t count, const void* tw, const int32_t* idx,
+                            int32_t* status, cudaStream_t stream) {
     switch (log2n) {
 #define LCT_CASE(L) \
-    case L: return launch_one<L, R>(in, out, desc, desc_step, count, tw, stream);
+    case L: return launch_one<L, R>(in, out, desc, desc_step, count, tw, idx, status, stream);
         LCT_CASE(1) LCT_CASE(2) LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6)
         LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12)
         LCT_CASE(13)
 #undef LCT_CASE
         case 14:
-            if constexpr (sizeof(R) == 4) return launch_one<14, R>(in, out, desc, desc_step, count, tw, stream);
+            if constexpr (sizeof(R) == 4)
+                return launch_one<14, R>(in, out, desc, desc_step, count, tw, idx, status, stream);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
@@ -266,8 +277,9 @@ bool lct_fused_supported(int dtype, int log2n) {
 
 cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
                              const lct_desc* desc, int desc_step, int64_t count, const void* tw,
-                             cudaStream_t stream) {
+                             const int32_t* idx, int32_t* status, cudaStream_t stream) {
     if (dtype == 0)
-        return launch_dispatch<float>(log2n, in, out, desc, desc_step, count, tw, stream);
-    return launch_dispatch<double>(log2n, in, out, desc, desc_step, count, tw, stream);
+        return launch_dispatch<float>(log2n, in, out, desc, desc_step, count, tw, idx, status,
+                                      stream);
+    return launch_dispatch<double>(log2n, in, out, desc, desc_step, count, tw, idx, status, stream);
 }

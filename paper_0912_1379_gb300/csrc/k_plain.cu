@@ -13,22 +13,66 @@ __device__ __forceinline__ cpx<double> load_c128(const cpx<R>* p, int64_t i) {
 }
 
 // b = 0: G_j = scale e^{2 pi i [phi_out m_j^2 + c_out]} f_j
+// idx (may be null): signal s of this launch is descriptor idx[s] (ragged
+// groups of equal N); mismatching descriptors are skipped and flagged.
 template <class R>
 __global__ void k_diag(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
-                       const lct_desc* __restrict__ desc, int desc_step, int64_t count, int log2n) {
+                       const lct_desc* __restrict__ desc, int desc_step, int64_t count, int log2n,
+                       const int32_t* __restrict__ idx, int32_t* __restrict__ status) {
     const int64_t N = 1ll << log2n;
     const int64_t total = count * N;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t sig = t >> log2n;
         const int n = (int)(t & (N - 1));
-        const lct_desc& D = desc[desc_step ? sig : 0];
+        const lct_desc& D = desc[desc_step ? (idx ? idx[sig] : sig) : 0];
+        if (idx && (D.kind != LCT_KIND_DIAG || D.log2n != log2n || D.offset < 0)) {
+            if (n == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+            continue;
+        }
         const int64_t base = desc_step ? D.offset : sig * N;
         const uint32_t m2 = m_squared(n, (int)N);
-        cpx<double> w = expi_turn64(phase64(D.out_hi, D.out_lo, m2) + D.out_c);
-        cpx<double> f = load_c128(in, base + n);
-        cpx<double> g = cscale(cmul(f, w), D.scale);
-        out[base + n] = {(R)g.x, (R)g.y};
+        if constexpr (sizeof(R) == 4) {
+            const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
+            cpx<float> w = expi_turn32<true>(phase32(D.out_hi, m2) + off);
+            out[base + n] = cscale(cmul(in[base + n], w), (float)D.scale);
+        } else {
+            cpx<double> w = expi_turn64(phase64(D.out_hi, D.out_lo, m2) + D.out_c);
+            cpx<double> g = cscale(cmul(load_c128(in, base + n), w), D.scale);
+            out[base + n] = {(R)g.x, (R)g.y};
+        }
+    }
+}
+
+// b = 0 over a ragged list of descriptors, one CTA per signal.
+template <class R>
+__global__ void k_diag_ragged(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+                              const lct_desc* __restrict__ desc, const int32_t* __restrict__ idx,
+                              int64_t count, int32_t* __restrict__ status) {
+    for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
+        const lct_desc& D = desc[idx[s]];
+        if (D.kind != LCT_KIND_DIAG || D.log2n < 1 || D.log2n > 16 || D.offset < 0) {
+            if (threadIdx.x == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+            continue;
+        }
+        const int N = 1 << D.log2n;
+        if constexpr (sizeof(R) == 4) {
+            // complex64: FP32 arithmetic on the exact 32-bit turn fraction
+            const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
+            const float sc = (float)D.scale;
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                const uint32_t m2 = m_squared(n, N);
+                cpx<float> w = expi_turn32<true>(phase32(D.out_hi, m2) + off);
+                out[D.offset + n] = cscale(cmul(in[D.offset + n], w), sc);
+            }
+        } else {
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                const uint32_t m2 = m_squared(n, N);
+                cpx<double> w = expi_turn64(phase64(D.out_hi, D.out_lo, m2) + D.out_c);
+                cpx<double> g = cscale(cmul(load_c128(in, D.offset + n), w), D.scale);
+                out[D.offset + n] = {(R)g.x, (R)g.y};
+            }
+        }
     }
 }
 
@@ -85,15 +129,29 @@ unsigned grid_for(int64_t total, int threads) {
 
 cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,
                             const lct_desc* desc, int desc_step, int64_t count,
-                            cudaStream_t stream) {
+                            const int32_t* idx, int32_t* status, cudaStream_t stream) {
     const int64_t total = count << log2n;
     const int th = 256;
     if (dtype == 0)
         k_diag<float><<<grid_for(total, th), th, 0, stream>>>(
-            (const cpx<float>*)in, (cpx<float>*)out, desc, desc_step, count, log2n);
+            (const cpx<float>*)in, (cpx<float>*)out, desc, desc_step, count, log2n, idx, status);
     else
         k_diag<double><<<grid_for(total, th), th, 0, stream>>>(
-            (const cpx<double>*)in, (cpx<double>*)out, desc, desc_step, count, log2n);
+            (const cpx<double>*)in, (cpx<double>*)out, desc, desc_step, count, log2n, idx, status);
+    return cudaGetLastError();
+}
+
+cudaError_t lct_launch_diag_ragged(int dtype, const void* in, void* out, const lct_desc* desc,
+                                   const int32_t* idx, int64_t count, int32_t* status,
+                                   cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(count < 152 * 8 ? count : 152 * 8);
+    if (dtype == 0)
+        k_diag_ragged<float><<<grid, 256, 0, stream>>>((const cpx<float>*)in, (cpx<float>*)out,
+                                                       desc, idx, count, status);
+    else
+        k_diag_ragged<double><<<grid, 256, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out,
+                                                        desc, idx, count, status);
     return cudaGetLastError();
 }
 

@@ -299,6 +299,21 @@ struct lct_plan_s {
     bool fft_valid = false;
     int64_t fft_n = 0, fft_batch = 0;
     int variant = -1;               // -1: not chosen (cache or default 0)
+    // ragged execution (mixed N or kinds): groups of equal (N, kind), largest
+    // N first, each an index list into desc; run as one CUDA graph
+    struct group { int log2n, kind; int64_t count, idx_off; };
+    bool ragged = false;
+    std::vector<group> groups;
+    std::vector<int32_t> idx;       // concatenated index lists
+    int32_t* d_idx = nullptr;
+    static constexpr int kBranches = 4;
+    cudaStream_t cap = nullptr;
+    cudaStream_t side[kBranches] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBranches] = {};
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_in = nullptr;
+    void* g_out = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -373,9 +388,25 @@ void release_device(lct_plan p) {
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     if (p->fft_valid) cufftDestroy(p->fft);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (int b = 0; b < lct_plan_s::kBranches; ++b) {
+        if (p->side[b]) cudaStreamDestroy(p->side[b]);
+        if (p->ev_join[b]) cudaEventDestroy(p->ev_join[b]);
+        p->side[b] = nullptr;
+        p->ev_join[b] = nullptr;
+    }
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    p->cap = nullptr;
+    p->ev_fork = nullptr;
+    p->gexec = nullptr;
+    p->g_in = nullptr;
+    p->g_out = nullptr;
     cudaFree(p->d_desc);
     cudaFree(p->d_status);
     cudaFree(p->d_work);
+    cudaFree(p->d_idx);
+    p->d_idx = nullptr;
     if (cur != p->device && cur >= 0) cudaSetDevice(cur);
     p->fft_valid = false;
     p->d_desc = nullptr;
@@ -407,6 +438,17 @@ lct_status ensure_device(lct_plan p) {
         return LCT_ERR_CUDA;
     }
     p->device = dev;
+    if (p->ragged && !p->idx.empty()) {
+        const size_t ib = sizeof(int32_t) * p->idx.size();
+        if (cudaMalloc(&p->d_idx, ib) != cudaSuccess) {
+            release_device(p);
+            return LCT_ERR_OOM;
+        }
+        if (cudaMemcpy(p->d_idx, p->idx.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) {
+            release_device(p);
+            return LCT_ERR_CUDA;
+        }
+    }
     return LCT_OK;
 }
 
@@ -443,6 +485,27 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
         lct_status st = make_desc(N[s], abcd + 8 * s, offsets ? offsets[s] : 0, &p->desc[s]);
         if (st != LCT_OK) { delete p; return st; }
         if (N[s] != p->N0) p->N0 = 0;
+    }
+    bool mixed_kind = false;
+    for (int64_t s = 1; s < count; ++s)
+        if (p->desc[s].kind != p->desc[0].kind) mixed_kind = true;
+    if (is_batch && (p->N0 == 0 || mixed_kind)) {
+        // Group by (N, kind), largest N first.
+        p->ragged = true;
+        std::map<std::pair<int, int>, std::vector<int32_t>, std::greater<std::pair<int, int>>> by;
+        for (int64_t s = 0; s < count; ++s) {
+            const lct_desc& D = p->desc[s];
+            by[{D.log2n, D.kind}].push_back((int32_t)s);
+        }
+        for (auto& kv : by) {
+            lct_plan_s::group g;
+            g.log2n = kv.first.first;
+            g.kind = kv.first.second;
+            g.count = (int64_t)kv.second.size();
+            g.idx_off = (int64_t)p->idx.size();
+            p->idx.insert(p->idx.end(), kv.second.begin(), kv.second.end());
+            p->groups.push_back(g);
+        }
     }
     *out = p;
     return LCT_OK;
@@ -519,7 +582,7 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
         const void* twl = lct_twiddle_table(p->dtype, lm);
         if (!twl) return LCT_ERR_OOM;
         return from_cuda(lct_launch_cluster(p->dtype, log2n, in, out, p->d_desc, desc_step, batch,
-                                            twl, stream));
+                                            twl, nullptr, p->d_status, stream));
     }
     if (!lct_fused_supported(p->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
     const void* tw = lct_twiddle_table(p->dtype, log2n);
@@ -540,7 +603,93 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
         return from_cuda(lct_launch_fused_tma(p->dtype, log2n, in, out, p->d_desc, desc_step,
                                               batch, tw, p->d_status, variant == 2, stream));
     return from_cuda(lct_launch_fused(p->dtype, log2n, in, out, p->d_desc, desc_step, batch, tw,
+                                      nullptr, p->d_status, stream));
+}
+
+// Launch one group of a ragged plan on `stream`.
+lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, void* out,
+                        cudaStream_t stream) {
+    const int32_t* idx = p->d_idx + g.idx_off;
+    if (g.kind == LCT_KIND_DIAG)
+        return from_cuda(lct_launch_diag(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count, idx,
+                                         p->d_status, stream));
+    const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
+    const bool single = lct_fused_supported(p->dtype, g.log2n);
+    const int v = tune_lookup(p->dtype, g.log2n);
+    if (lm >= 0 && (!single || v == 5))
+        return from_cuda(lct_launch_cluster(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count,
+                                            lct_twiddle_table(p->dtype, lm), idx, p->d_status,
+                                            stream));
+    if (!single) return LCT_ERR_UNSUPPORTED;
+    return from_cuda(lct_launch_fused(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count,
+                                      lct_twiddle_table(p->dtype, g.log2n), idx, p->d_status,
                                       stream));
+}
+
+// Capture every group into one graph: a fork to kBranches streams, groups
+// dealt round-robin (largest N first), a join; instantiated once per
+// (in, out) pair.
+lct_status build_graph(lct_plan p, const void* in, void* out) {
+    // tables first: allocation is not allowed while capturing
+    for (const auto& g : p->groups) {
+        if (g.kind == LCT_KIND_DIAG) continue;
+        const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
+        if (lm >= 0 && !lct_twiddle_table(p->dtype, lm)) return LCT_ERR_OOM;
+        if (g.log2n >= 5 && lct_fused_supported(p->dtype, g.log2n) &&
+            !lct_twiddle_table(p->dtype, g.log2n))
+            return LCT_ERR_OOM;
+    }
+    if (!p->cap) {
+        if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+            return LCT_ERR_CUDA;
+        for (int b = 0; b < lct_plan_s::kBranches; ++b)
+            if (cudaStreamCreateWithFlags(&p->side[b], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_join[b], cudaEventDisableTiming) != cudaSuccess)
+                return LCT_ERR_CUDA;
+    }
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return LCT_ERR_CUDA;
+    lct_status st = LCT_OK;
+    if (cudaEventRecord(p->ev_fork, p->cap) != cudaSuccess) st = LCT_ERR_CUDA;
+    for (int b = 0; b < lct_plan_s::kBranches && st == LCT_OK; ++b)
+        if (cudaStreamWaitEvent(p->side[b], p->ev_fork, 0) != cudaSuccess) st = LCT_ERR_CUDA;
+    for (size_t k = 0; k < p->groups.size() && st == LCT_OK; ++k)
+        st = launch_group(p, p->groups[k], in, out, p->side[k % lct_plan_s::kBranches]);
+    for (int b = 0; b < lct_plan_s::kBranches && st == LCT_OK; ++b) {
+        if (cudaEventRecord(p->ev_join[b], p->side[b]) != cudaSuccess ||
+            cudaStreamWaitEvent(p->cap, p->ev_join[b], 0) != cudaSuccess)
+            st = LCT_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+    if (st != LCT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess || !graph) return LCT_ERR_CUDA;
+    const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        p->gexec = nullptr;
+        return LCT_ERR_CUDA;
+    }
+    p->g_in = in;
+    p->g_out = out;
+    return LCT_OK;
+}
+
+lct_status run_ragged(lct_plan p, const void* in, void* out, cudaStream_t stream) {
+    if (p->prec != LCT_PREC_NATIVE) return LCT_ERR_UNSUPPORTED;
+    if (!p->gexec || p->g_in != in || p->g_out != out) {
+        lct_status st = build_graph(p, in, out);
+        if (st != LCT_OK) return st;
+    }
+    return from_cuda(cudaGraphLaunch(p->gexec, stream));
 }
 
 }  // namespace
@@ -670,16 +819,12 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
     st = ensure_device(plan);
     if (st != LCT_OK) return st;
     int desc_step = plan->is_batch ? 1 : 0;
-    if (plan->N0 == 0) return LCT_ERR_UNSUPPORTED;     // ragged batch: not yet
+    if (plan->ragged) return run_ragged(plan, in, out, stream);
     const lct_desc& D0 = plan->desc[0];
-    if (plan->is_batch) {
-        for (const lct_desc& D : plan->desc)
-            if (D.kind != D0.kind) return LCT_ERR_UNSUPPORTED;
-    }
     int log2n = D0.log2n;
     if (D0.kind == LCT_KIND_DIAG)
         return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
-                                         batch, stream));
+                                         batch, nullptr, plan->d_status, stream));
     if (plan->prec == LCT_PREC_PLAIN64) {
         if (plan->is_batch) {
             // the plain path assumes contiguous rows

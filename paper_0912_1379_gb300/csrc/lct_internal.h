@@ -64,9 +64,12 @@ const void* lct_twiddle_table_pair(int log2n);
 // desc_step = 1: desc[s] for signal s (its own offset).
 // dtype: 0 = complex64 (FP32 arithmetic), 1 = complex128 (FP64 arithmetic).
 // tw: the twiddle table of lct_twiddle_table(dtype, log2n).
+// idx (may be null): ragged mode, signal s of the launch is descriptor
+// idx[s] (desc_step must be 1); descriptors that do not match the kernel's N
+// or kind are skipped and LCT_DEV_BAD_DESC is recorded in *status.
 cudaError_t lct_launch_fused(int dtype, int log2n, const void* in, void* out,
                              const lct_desc* desc, int desc_step, int64_t count, const void* tw,
-                             cudaStream_t stream);
+                             const int32_t* idx, int32_t* status, cudaStream_t stream);
 bool lct_fused_supported(int dtype, int log2n);
 
 // Large-N fused kernel (N = 16384 .. 65536, both dtypes): a thread-block
@@ -75,7 +78,8 @@ bool lct_fused_supported(int dtype, int log2n);
 int lct_cluster_local_log2(int dtype, int log2n);     // -1 if unsupported
 cudaError_t lct_launch_cluster(int dtype, int log2n, const void* in, void* out,
                                const lct_desc* desc, int desc_step, int64_t count,
-                               const void* tw_local, cudaStream_t stream);
+                               const void* tw_local, const int32_t* idx, int32_t* status,
+                               cudaStream_t stream);
 
 // Persistent variant of the fused kernel with bulk-async prefetch of the next
 // signal group (complex64, N = 256 .. 8192).  Signal starts must be 16-byte
@@ -101,10 +105,17 @@ cudaError_t lct_launch_fused_pair_tma(int dtype, int log2n, const void* in, void
                                       const void* tw_pair, int32_t* status, cudaStream_t stream);
 bool lct_fused_pair_tma_supported(int dtype, int log2n);
 
-// Diagonal branch (b == 0) for `count` signals of N = 2^log2n.
+// Diagonal branch (b == 0) for `count` signals of N = 2^log2n; idx as for
+// lct_launch_fused (may be null).
 cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,
                             const lct_desc* desc, int desc_step, int64_t count,
-                            cudaStream_t stream);
+                            const int32_t* idx, int32_t* status, cudaStream_t stream);
+
+// Diagonal branch (b == 0) over a ragged list: descriptors idx[0..count),
+// any N; one CTA per signal.  Mismatching descriptors set LCT_DEV_BAD_DESC.
+cudaError_t lct_launch_diag_ragged(int dtype, const void* in, void* out, const lct_desc* desc,
+                                   const int32_t* idx, int64_t count, int32_t* status,
+                                   cudaStream_t stream);
 
 // Plain FP64 baseline pieces.  work: complex128 [count][N].
 cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,

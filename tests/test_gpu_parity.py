@@ -248,3 +248,120 @@ def test_full_size_uniform_4096():
         p.destroy()
     ref = O.lct(f[idx].astype(np.complex128), params[idx])
     assert rel_l2(G, ref).max() < TOL32
+
+
+# --------------------------------------------------------------------------
+# ragged batches: mixed N and kinds in one plan, one CUDA-graph launch
+# --------------------------------------------------------------------------
+def _ragged_case(specs, seed, gap=3):
+    """specs: list of (log2n, kind, abcd or z). Returns N, abcd (complex),
+    offsets (with gaps), packed input (complex64) and the per-signal inputs."""
+    rng = np.random.default_rng(seed)
+    Ns, abcds, offs, sigs = [], [], [], []
+    off = 0
+    for log2n, kind, par in specs:
+        N = 1 << log2n
+        if kind == "frft":
+            abcd = O.abcd_of_z(par)
+        else:
+            abcd = np.asarray(par, dtype=np.complex128)
+        x = O.nodes(N)
+        f = (np.exp(-x * x / 8) * np.exp(0.3j * x * x)
+             + 1e-3 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))).astype(np.complex64)
+        Ns.append(N); abcds.append(abcd); offs.append(off); sigs.append(f)
+        off += N + gap * 2                      # even gaps keep 16-byte alignment optional
+    buf = np.zeros(off, dtype=np.complex64)
+    for o, f in zip(offs, sigs):
+        buf[o:o + len(f)] = f
+    return np.array(Ns), np.array(abcds), np.array(offs), buf, sigs
+
+
+RAGGED_SPECS = [
+    (16, "lct", (0.4, 1.3, (0.4 * -0.7 - 1) / 1.3, -0.7)),
+    (10, "frft", 0.6 * np.exp(1.1j)),
+    (6, "lct", (0.0, 1.0, -1.0, 0.0)),
+    (12, "b0", (1 / 1.4, 0.0, 0.7, 1.4)),
+    (15, "lct", (-1.2, -0.5, (-1.2 * 0.9 - 1) / -0.5, 0.9)),
+    (8, "frft", 0.35 * np.exp(-2.0j)),
+    (12, "lct", (1.1, 0.8, (1.1 * 0.3 - 1) / 0.8, 0.3)),
+    (10, "lct", (0.0, 1.0, -1.0, 0.0)),
+    (7, "b0", (1 / 0.6, 0.0, -1.5, 0.6)),
+    (14, "lct", (0.2, 1.9, (0.2 * 1.5 - 1) / 1.9, 1.5)),
+    (12, "frft", 0.9 * np.exp(0.4j)),
+    (9, "lct", (1.7, -1.1, (1.7 * 0.2 - 1) / -1.1, 0.2)),
+]
+
+
+def test_ragged_mixed_sizes_and_kinds():
+    Ns, abcds, offs, buf, sigs = _ragged_case(RAGGED_SPECS, seed=31)
+    p = lct.Plan.batch(Ns, abcds, offs, dtype=lct.LCT_C64)
+    try:
+        x = torch.from_numpy(buf).cuda()
+        out = torch.zeros_like(x)
+        lct.lct_execute(p.handle, x, out, len(Ns))
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        G = out.cpu().numpy()
+        # a second buffer pair: the graph is captured again for the new pointers
+        x2 = torch.from_numpy(buf[::-1].copy()[::-1].copy()).cuda()
+        out2 = torch.zeros_like(x2)
+        lct.lct_execute(p.handle, x2, out2, len(Ns))
+        torch.cuda.synchronize()
+        G2 = out2.cpu().numpy()
+    finally:
+        p.destroy()
+    assert np.array_equal(G, G2)
+    for N, abcd, o, f in zip(Ns, abcds, offs, sigs):
+        ref = O.lct(f.astype(np.complex128), abcd)
+        assert rel_l2(G[o:o + N], ref) < TOL32, (N, abcd)
+    # the gaps between signals are untouched
+    mask = np.ones(len(buf), dtype=bool)
+    for N, o in zip(Ns, offs):
+        mask[o:o + N] = False
+    assert np.all(G[mask] == 0)
+
+
+def test_ragged_full_size_workload():
+    """The 20000-instance ragged workload (N = 2^6..2^16, four kinds), one
+    graph launch; parity on a sample of signals, Parseval on all real ones."""
+    r = W.ragged_plan()
+    M = len(r["kind"])
+    Ns = (1 << r["log2n"]).astype(np.int64)
+    abcd = r["abcd"].copy()
+    fr = r["kind"] == W.KIND_FRFT
+    for s in np.nonzero(fr)[0]:
+        abcd[s] = O.abcd_of_z(r["z"][s])
+    offs = np.concatenate([[0], np.cumsum(Ns)[:-1]]).astype(np.int64)
+    total = int(Ns.sum())
+    buf = np.empty(total, dtype=np.complex64)
+    rng = r["rng"]
+    for s in range(M):
+        x = O.nodes(int(Ns[s]))
+        buf[offs[s]:offs[s] + Ns[s]] = W.ragged_signal(x, r["s"][s], r["q"][s], rng)
+    p = lct.Plan.batch(Ns, abcd, offs, dtype=lct.LCT_C64)
+    try:
+        xin = torch.from_numpy(buf).cuda()
+        out = torch.empty_like(xin)
+        lct.lct_execute(p.handle, xin, out, M)
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        G = out.cpu().numpy()
+    finally:
+        p.destroy()
+    # sample: a few signals of every kind, small and mid sizes
+    checked = 0
+    for kind in range(4):
+        ids = [s for s in np.nonzero(r["kind"] == kind)[0] if Ns[s] <= 4096][:6]
+        for s in ids:
+            o, N = offs[s], Ns[s]
+            ref = O.lct(buf[o:o + N].astype(np.complex128), abcd[s])
+            assert rel_l2(G[o:o + N], ref) < TOL32, (kind, N)
+            checked += 1
+    assert checked >= 20
+    # scaled Parseval for every real-parameter signal with b != 0
+    for s in np.nonzero((r["kind"] == W.KIND_GENERIC) | (r["kind"] == W.KIND_FOURIER))[0]:
+        o, N = offs[s], Ns[s]
+        b = abs(abcd[s][1])
+        lhs = np.sum(np.abs(G[o:o + N].astype(np.complex128)) ** 2) * 4 * b / np.pi
+        rhs = np.sum(np.abs(buf[o:o + N].astype(np.complex128)) ** 2)
+        assert abs(lhs / rhs - 1) < 2e-5
