@@ -154,6 +154,43 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                         int64_t batch, lct_dtype dtype, lct_stream_t stream);
 
+/* Backward pass of lct_execute (spec differentiation; the chain rule
+ * on L = S1 F S2 of Sec. 3).  grad_out: cotangent g = dl/dRe G + i dl/dIm G
+ * (PyTorch's convention for a real loss l); writes grad_in = L^H g, the
+ * adjoint transform (conjugated chirps, inverse-sign DFT).  If grad_abd is
+ * not NULL it also writes the parameter gradients (dl/da, dl/db, dl/dd) --
+ * c is not a free parameter when b != 0 -- computed from the dense-matrix
+ * derivative with the output points y_j = 4 b x_j / pi moving with b:
+ * 3 doubles per signal for batch plans, 3 doubles summed over `batch` for
+ * single plans; `in` (f) and `out` (G) of the forward call are then
+ * required.  All pointers are device memory.  Supported: uniform N <= 4096,
+ * b != 0; parameter gradients for real parameters only
+ * (LCT_ERR_UNSUPPORTED otherwise).  The plan keeps a workspace of 3 doubles
+ * per signal for the reductions. */
+lct_status lct_backward(lct_plan plan, const void* grad_out, const void* in, const void* out,
+                        void* grad_in, double* grad_abd, int64_t batch, lct_stream_t stream);
+
+/* Separable 2-D LCT (fields [batch][ny][nx], row-major): the 1-D transform
+ * with abcd_x (4 reals) along every row (length nx), then with abcd_y along
+ * every column (length ny).  Output points: the 1-D grids of each axis.
+ * nx, ny powers of two in [128 (256 for complex128), 4096]; b != 0 on both
+ * axes.  Host-only creation. */
+typedef struct lct2d_plan_s* lct2d_plan;
+lct_status lct2d_plan_create(lct2d_plan* out, int64_t ny, int64_t nx, const double abcd_y[4],
+                             const double abcd_x[4], lct_dtype dtype);
+/* mid receives the row-transformed fields (kept for lct2d_backward; mid ==
+ * out is allowed when no backward pass follows). */
+lct_status lct2d_execute(lct2d_plan plan, const void* in, void* mid, void* out, int64_t batch,
+                         lct_stream_t stream);
+/* Backward of lct2d_execute: grad_in = (L_y (x) L_x)^H grad_out, using the
+ * caller's scratch field grad_mid; grad_abd (may be NULL) receives 6 doubles
+ * summed over the batch: (dl/da, dl/db, dl/dd) of the x axis, then of the
+ * y axis.  in, mid, out: the buffers of the forward call. */
+lct_status lct2d_backward(lct2d_plan plan, const void* grad_out, const void* in, const void* mid,
+                          const void* out, void* grad_mid, void* grad_in, double* grad_abd,
+                          int64_t batch, lct_stream_t stream);
+lct_status lct2d_plan_destroy(lct2d_plan plan);
+
 /* Output points and rho of signal `index` of the plan (0 for single plans):
  * y_reim receives N complex points (2N doubles), rho N doubles (may be
  * NULL).  Host-only. */

@@ -73,6 +73,11 @@ def _load():
             "lct_plan_set_variant": [vp, i32],
             "lct_plan_get_variant": [vp, ctypes.POINTER(i32)],
             "lct_plan_autotune": [vp, vp, vp, i64, vp],
+            "lct_backward": [vp, vp, vp, vp, vp, vp, i64, vp],
+            "lct2d_plan_create": [plan_p, i64, i64, dp, dp, i32],
+            "lct2d_execute": [vp, vp, vp, vp, i64, vp],
+            "lct2d_backward": [vp, vp, vp, vp, vp, vp, vp, vp, i64, vp],
+            "lct2d_plan_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -106,6 +111,8 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 def _ptr(t) -> int:
+    if t is None:
+        return 0
     if isinstance(t, int):
         return t
     return t.data_ptr()
@@ -179,6 +186,41 @@ def lct_plan_autotune(plan: int, inp, out, batch: int, stream=None) -> int:
 def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
     _check(_load().lct_execute(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
            "lct_execute")
+
+
+def lct_backward(plan: int, grad_out, inp, out, grad_in, grad_abd, batch: int, stream=None) -> None:
+    """grad_in = L^H grad_out; grad_abd (float64 device tensor or None)
+    receives (dl/da, dl/db, dl/dd) per signal (batch plans) or summed."""
+    _check(_load().lct_backward(plan, _ptr(grad_out), _ptr(inp), _ptr(out), _ptr(grad_in),
+                                _ptr(grad_abd), batch, _stream_handle(stream)), "lct_backward")
+
+
+def lct2d_plan_create(ny: int, nx: int, abcd_y, abcd_x, dtype: int = LCT_C64) -> int:
+    py = np.ascontiguousarray(np.asarray(abcd_y, dtype=np.float64))
+    px = np.ascontiguousarray(np.asarray(abcd_x, dtype=np.float64))
+    if py.shape != (4,) or px.shape != (4,):
+        raise ValueError("abcd_x and abcd_y must hold 4 real values")
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_load().lct2d_plan_create(ctypes.byref(h), ny, nx, py.ctypes.data_as(dp),
+                                     px.ctypes.data_as(dp), dtype), "lct2d_plan_create")
+    return h.value
+
+
+def lct2d_execute(plan: int, inp, mid, out, batch: int, stream=None) -> None:
+    _check(_load().lct2d_execute(plan, _ptr(inp), _ptr(mid), _ptr(out), batch,
+                                 _stream_handle(stream)), "lct2d_execute")
+
+
+def lct2d_backward(plan: int, grad_out, inp, mid, out, grad_mid, grad_in, grad_abd, batch: int,
+                   stream=None) -> None:
+    _check(_load().lct2d_backward(plan, _ptr(grad_out), _ptr(inp), _ptr(mid), _ptr(out),
+                                  _ptr(grad_mid), _ptr(grad_in), _ptr(grad_abd), batch,
+                                  _stream_handle(stream)), "lct2d_backward")
+
+
+def lct2d_plan_destroy(plan: int) -> None:
+    _check(_load().lct2d_plan_destroy(plan), "lct2d_plan_destroy")
 
 
 def frft_execute(N: int, z: complex, inp, out, batch: int, dtype: int = LCT_C64, stream=None) -> None:
@@ -289,3 +331,131 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+class Plan2D:
+    """Owning wrapper of an lct2d_plan handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def destroy(self) -> None:
+        if self.handle:
+            lct2d_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# autograd: the library's forward and backward kernels as torch Functions
+# ---------------------------------------------------------------------------
+def _torch_fns():
+    import torch
+
+    class LCTFunction(torch.autograd.Function):
+        """G = LCT(x) for x [batch, N] complex (cuda); abcd float64 [4]
+        (shared) or [batch, 4] (per signal).  Backward: lct_backward."""
+
+        @staticmethod
+        def forward(ctx, x, abcd):
+            x = x.contiguous()
+            code = dtype_code(x.dtype)
+            xb = x.reshape(-1, x.shape[-1])
+            batch, N = xb.shape
+            p = abcd.detach().to("cpu", torch.float64).numpy()
+            if p.ndim == 1:
+                plan = Plan(lct_plan_create(N, *[float(v) for v in p], code), N, code)
+            else:
+                plan = Plan(lct_plan_create_batch([N] * batch, p, np.arange(batch) * N, code), N, code)
+            out = torch.empty_like(xb)
+            plan.execute(xb, out, batch)
+            ctx.plan, ctx.batch, ctx.shape, ctx.pshape = plan, batch, x.shape, p.shape
+            ctx.pdev = abcd.device
+            ctx.save_for_backward(xb, out)
+            return out.reshape(x.shape)
+
+        @staticmethod
+        def backward(ctx, g):
+            xb, out = ctx.saved_tensors
+            g = g.contiguous().reshape(xb.shape)
+            grad_in = torch.empty_like(xb)
+            want_p = ctx.needs_input_grad[1]
+            gp = None
+            if want_p:
+                gp = torch.zeros((ctx.batch, 3) if len(ctx.pshape) == 2 else (3,),
+                                 dtype=torch.float64, device=xb.device)
+            lct_backward(ctx.plan.handle, g, xb, out, grad_in, gp, ctx.batch)
+            grad_abcd = None
+            if want_p:
+                z = torch.zeros_like(gp[..., :1])
+                grad_abcd = torch.cat([gp[..., 0:2], z, gp[..., 2:3]], dim=-1)   # c: no effect for b != 0
+                grad_abcd = grad_abcd.to(ctx.pdev)
+            # the plan lives as long as ctx: backward may run more than once
+            # (retain_graph), and Plan.__del__ frees it afterwards
+            return grad_in.reshape(ctx.shape), grad_abcd
+
+    class LCT2DFunction(torch.autograd.Function):
+        """Separable 2-D LCT of x [batch, ny, nx]: rows with abcd_x, then
+        columns with abcd_y (float64 [4] each).  Backward: lct2d_backward."""
+
+        @staticmethod
+        def forward(ctx, x, abcd_x, abcd_y):
+            x = x.contiguous()
+            code = dtype_code(x.dtype)
+            xb = x.reshape(-1, x.shape[-2], x.shape[-1])
+            batch, ny, nx = xb.shape
+            px = abcd_x.detach().to("cpu", torch.float64).numpy()
+            py = abcd_y.detach().to("cpu", torch.float64).numpy()
+            plan = Plan2D(lct2d_plan_create(ny, nx, py, px, code))
+            mid = torch.empty_like(xb)
+            out = torch.empty_like(xb)
+            lct2d_execute(plan.handle, xb, mid, out, batch)
+            ctx.plan, ctx.batch, ctx.shape = plan, batch, x.shape
+            ctx.pdev = (abcd_x.device, abcd_y.device)
+            ctx.save_for_backward(xb, mid, out)
+            return out.reshape(x.shape)
+
+        @staticmethod
+        def backward(ctx, g):
+            xb, mid, out = ctx.saved_tensors
+            g = g.contiguous().reshape(xb.shape)
+            grad_mid = torch.empty_like(xb)
+            grad_in = torch.empty_like(xb)
+            want_p = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+            gp = torch.zeros(6, dtype=torch.float64, device=xb.device) if want_p else None
+            lct2d_backward(ctx.plan.handle, g, xb, mid, out, grad_mid, grad_in, gp, ctx.batch)
+            gx = gy = None
+            if want_p:
+                z = torch.zeros(1, dtype=torch.float64, device=xb.device)
+                gx = torch.cat([gp[0:2], z, gp[2:3]]).to(ctx.pdev[0])
+                gy = torch.cat([gp[3:5], z, gp[5:6]]).to(ctx.pdev[1])
+            return grad_in.reshape(ctx.shape), gx, gy
+
+    return LCTFunction, LCT2DFunction
+
+
+_FNS = None
+
+
+def _fns():
+    global _FNS
+    if _FNS is None:
+        _FNS = _torch_fns()
+    return _FNS
+
+
+def lct(x, abcd):
+    """Differentiable LCT of the last axis of x (complex64/128 cuda tensor).
+    abcd: float64 tensor [4] or [batch, 4] with ad - bc = 1 (b != 0 for
+    gradients); gradients flow to x and to (a, b, d)."""
+    return _fns()[0].apply(x, abcd)
+
+
+def lct2d(x, abcd_x, abcd_y):
+    """Differentiable separable 2-D LCT of x [..., ny, nx]."""
+    return _fns()[1].apply(x, abcd_x, abcd_y)

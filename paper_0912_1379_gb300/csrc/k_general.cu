@@ -1,0 +1,325 @@
+// General single-CTA XFT kernel: forward or adjoint transform, rows or
+// columns, with optional parameter-gradient sums.  Used by lct_backward
+// (adjoint + gradients) and by the separable 2-D transform (columns).
+//
+// Adjoint (Sec. 3: L = S1 F S2, so L^H = S2^H F^H S1^H): the input is
+// multiplied by conj(post-chirp) * scale, the DFT runs with the inverse sign
+// e^{+2 pi i jk/N}, and the output by conj(pre-chirp) (including the real
+// factor e^{-decay m^2} of complex parameters).
+//
+// Gradient sums (real parameters, b != 0), per signal, with g the cotangent
+// dl/dRe G + i dl/dIm G, G the forward output, f the forward input and
+// h = L^H g:
+//   SA = sum_k m_k^2 Im(conj(h_k) f_k)
+//   SR = sum_j Re(conj(g_j) G_j)
+//   SG = sum_j m_j^2 Im(conj(g_j) G_j)
+// from which dl/da, dl/db, dl/dd follow linearly (lct_grad_finalize): with
+// x^2 = pi^2 m^2 / (8N) the derivatives of
+//   L_jk = dx (2 pi i b)^{-1/2} e^{i 8 b d x_j^2/pi^2} e^{-i 4 x_j x_k / pi} e^{i a x_k^2/(2b)}
+// give dl/da = -pi^2/(16 b N) SA,  dl/dd = -(b/N) SG,
+//      dl/db = a pi^2/(16 b^2 N) SA - SR/(2b) - (d/N) SG.
+//
+// Layout: signal s starts at D.offset (batch plans) or at
+// (s / P) * big + (s % P), with element stride es.  Rows: P = 1, big = N,
+// es = 1.  Columns of a [fields][N][W] array: P = W, big = N W, es = W; then
+// G = 4 (complex64) or 2 (complex128) adjacent columns share a CTA with
+// interleaved lanes so that every warp access covers whole 32-byte sectors.
+#include "xft_engine.cuh"
+#include "xft_chirp.cuh"
+
+namespace {
+
+using namespace xft;
+
+template <int L, class R>
+__device__ __forceinline__ cpx<R> pre_g(const lct_desc& D, int n, bool decay) {
+    if constexpr (sizeof(R) == 4) return pre_chirp<L>(D, n, decay);
+    else return pre_chirp64<L>(D, n, decay);
+}
+template <int L, class R>
+__device__ __forceinline__ cpx<R> post_g(const lct_desc& D, int n) {
+    if constexpr (sizeof(R) == 4) return post_chirp<L>(D, n);
+    else return post_chirp64<L>(D, n);
+}
+template <class R>
+__device__ __forceinline__ cpx<R> conj_of(cpx<R> a) { return {a.x, -a.y}; }
+
+// Signals per CTA: interleaved columns (G) or, for rows, enough signals to
+// fill 256 threads.
+template <int L, int G>
+struct gen_shape {
+    static constexpr int T = shape<L>::T;
+    static constexpr int SPC = G > 1 ? G : (T >= 256 ? 1 : 256 / T);
+    static constexpr int THREADS = T * SPC;
+};
+
+// 768 resident threads (complex64, <= 85 registers) / 512 (complex128, 128).
+template <int L, class R, int G>
+constexpr int gen_min_blocks() {
+    constexpr int per_sm = sizeof(R) == 4 ? 768 : 512;
+    constexpr int b = per_sm / gen_shape<L, G>::THREADS;
+    return b < 1 ? 1 : (b > 16 ? 16 : b);
+}
+
+template <int L, class R, int G, bool ADJ, bool GRAD>
+__global__ void __launch_bounds__(gen_shape<L, G>::THREADS, (gen_min_blocks<L, R, G>()))
+k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+          const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+          const cpx<R>* __restrict__ tw, int64_t es, int64_t P, int64_t big,
+          const cpx<R>* __restrict__ fwd_out, const cpx<R>* __restrict__ fwd_in,
+          double* __restrict__ partial) {
+    using S = shape<L>;
+    using F = gen_shape<L, G>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int sl = G > 1 ? tid % G : tid / S::T;
+    const int i = G > 1 ? tid / G : tid - sl * S::T;
+    const int64_t sig = (int64_t)blockIdx.x * F::SPC + sl;
+    const bool active = sig < count;
+    const lct_desc D = desc[desc_step && active ? sig : 0];
+    // rows: unit stride, signal s at s * big; columns: (s / P) * big + (s % P), stride es
+    const int64_t base = desc_step ? D.offset : (G > 1 ? (sig / P) * big + (sig % P) : sig * big);
+    const int64_t est = G > 1 ? es : 1;
+    cpx<R>* buf = smem + sl * S::NP;
+    const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+    const R sc = (R)D.scale;
+
+    R sa = 0, sr = 0, sg = 0;                 // sums in the sample precision
+    cpx<R> v[S::E];
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const int n = i + e * S::T;
+        const int64_t at = base + (int64_t)n * est;
+        cpx<R> x = {R(0), R(0)};
+        if (active) x = ld_stream(in + at);
+        if (ADJ) {
+            if (GRAD && active) {
+                const cpx<R> Gv = fwd_out[at];
+                sr += x.x * Gv.x + x.y * Gv.y;                              // Re(conj(g) G)
+                sg += (R)m_squared(n, S::N) * (x.x * Gv.y - x.y * Gv.x);     // m^2 Im(conj(g) G)
+            }
+            v[e] = cscale(cmul(x, conj_of(post_g<L, R>(D, n))), sc);
+        } else {
+            v[e] = cmul(x, pre_g<L, R>(D, n, decay));
+        }
+    }
+    dft_signal<L, ADJ ? 1 : -1>(v, buf, i, tw);
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int n = i + e * S::T;
+            const int64_t at = base + (int64_t)n * est;
+            cpx<R> y;
+            if (ADJ) {
+                y = cmul(v[e], conj_of(pre_g<L, R>(D, n, decay)));
+                if (GRAD) {
+                    const cpx<R> fv = fwd_in[at];
+                    sa += (R)m_squared(n, S::N) * (y.x * fv.y - y.y * fv.x);  // m^2 Im(conj(h) f)
+                }
+            } else {
+                y = cscale(cmul(v[e], post_g<L, R>(D, n)), sc);
+            }
+            out[at] = y;
+        }
+    }
+    if (GRAD) {
+        // Reduce (sa, sr, sg) over the threads of each signal: shuffles
+        // within a warp (sample precision), then the warps' partials in double.
+        constexpr int SEG = G > 1 ? 32 : (S::T < 32 ? S::T : 32);   // lanes of one signal per warp
+        if (G > 1) {
+#pragma unroll
+            for (int o = 16; o >= G; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                sg += __shfl_xor_sync(0xffffffffu, sg, o);
+            }
+        } else {
+#pragma unroll
+            for (int o = SEG / 2; o >= 1; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                sg += __shfl_xor_sync(0xffffffffu, sg, o);
+            }
+        }
+        const int lane = tid & 31, warp = tid >> 5;
+        if (G == 1 && S::T <= 32) {
+            // every signal lies inside one warp: its first lane holds the total
+            if (i == 0 && active) {
+                partial[3 * sig + 0] = sa;
+                partial[3 * sig + 1] = sr;
+                partial[3 * sig + 2] = sg;
+            }
+        } else {
+            __syncthreads();                   // shared memory free for the partials
+            double* red = reinterpret_cast<double*>(smem_raw);
+            constexpr int NW = F::THREADS / 32;
+            if (G > 1) {
+                if (lane < G) {
+                    red[3 * (warp * G + lane) + 0] = sa;
+                    red[3 * (warp * G + lane) + 1] = sr;
+                    red[3 * (warp * G + lane) + 2] = sg;
+                }
+            } else if (lane == 0) {
+                red[3 * warp + 0] = sa;
+                red[3 * warp + 1] = sr;
+                red[3 * warp + 2] = sg;
+            }
+            __syncthreads();
+            if (i == 0 && active) {
+                double a = 0, r = 0, g = 0;
+                if (G > 1) {
+                    for (int w = 0; w < NW; ++w) {
+                        a += red[3 * (w * G + sl) + 0];
+                        r += red[3 * (w * G + sl) + 1];
+                        g += red[3 * (w * G + sl) + 2];
+                    }
+                } else {
+                    const int w0 = (sl * S::T) >> 5, nw = S::T >> 5;
+                    for (int w = w0; w < w0 + nw; ++w) {
+                        a += red[3 * w + 0];
+                        r += red[3 * w + 1];
+                        g += red[3 * w + 2];
+                    }
+                }
+                partial[3 * sig + 0] = a;
+                partial[3 * sig + 1] = r;
+                partial[3 * sig + 2] = g;
+            }
+        }
+    }
+}
+
+template <int L, class R, int G, bool ADJ, bool GRAD>
+cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc_step,
+                       int64_t count, const void* tw, int64_t es, int64_t P, int64_t big,
+                       const void* fwd_out, const void* fwd_in, double* partial,
+                       cudaStream_t stream) {
+    using S = shape<L>;
+    using F = gen_shape<L, G>;
+    size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
+    if (GRAD && smem < (size_t)F::THREADS / 32 * 4 * 3 * sizeof(double) + 64)
+        smem = (size_t)F::THREADS / 32 * 4 * 3 * sizeof(double) + 64;
+    auto kern = k_xft_gen<L, R, G, ADJ, GRAD>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (count + F::SPC - 1) / F::SPC;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)blocks, F::THREADS, smem, stream>>>(
+        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw, es, P, big,
+        (const cpx<R>*)fwd_out, (const cpx<R>*)fwd_in, partial);
+    return cudaGetLastError();
+}
+
+template <class R, int G, bool ADJ, bool GRAD>
+cudaError_t gen_dispatch(int log2n, const void* in, void* out, const lct_desc* desc, int desc_step,
+                         int64_t count, const void* tw, int64_t es, int64_t P, int64_t big,
+                         const void* fo, const void* fi, double* partial, cudaStream_t stream) {
+    switch (log2n) {
+#define LCT_CASE(L)                                                                           \
+    case L:                                                                                   \
+        return launch_gen<L, R, G, ADJ, GRAD>(in, out, desc, desc_step, count, tw, es, P, big, \
+                                             fo, fi, partial, stream);
+        LCT_CASE(1) LCT_CASE(2) LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6)
+        LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12)
+#undef LCT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class R, int G>
+cudaError_t gen_mode(int log2n, bool adj, bool grad, const void* in, void* out,
+                     const lct_desc* desc, int desc_step, int64_t count, const void* tw, int64_t es,
+                     int64_t P, int64_t big, const void* fo, const void* fi, double* partial,
+                     cudaStream_t stream) {
+    if (!adj)
+        return gen_dispatch<R, G, false, false>(log2n, in, out, desc, desc_step, count, tw, es, P,
+                                                big, fo, fi, partial, stream);
+    if (!grad)
+        return gen_dispatch<R, G, true, false>(log2n, in, out, desc, desc_step, count, tw, es, P,
+                                               big, fo, fi, partial, stream);
+    return gen_dispatch<R, G, true, true>(log2n, in, out, desc, desc_step, count, tw, es, P, big,
+                                          fo, fi, partial, stream);
+}
+
+// dl/da, dl/db, dl/dd from the sums (SA, SR, SG); coef: per signal
+// (cA_a, cA_b, cR_b, cG_b, cG_d).  shared != 0: one parameter set for all
+// signals, the sums are added first and grad has 3 entries.
+__global__ void k_grad_finalize(const double* __restrict__ partial, const double* __restrict__ coef,
+                                int coef_step, int64_t count, int shared, double* __restrict__ grad) {
+    if (!shared) {
+        for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < count;
+             s += (int64_t)gridDim.x * blockDim.x) {
+            const double* c = coef + 5 * (coef_step ? s : 0);
+            const double SA = partial[3 * s], SR = partial[3 * s + 1], SG = partial[3 * s + 2];
+            grad[3 * s + 0] = c[0] * SA;
+            grad[3 * s + 1] = c[1] * SA + c[2] * SR + c[3] * SG;
+            grad[3 * s + 2] = c[4] * SG;
+        }
+        return;
+    }
+    __shared__ double red[3][256];
+    double a = 0, r = 0, g = 0;
+    for (int64_t s = threadIdx.x; s < count; s += blockDim.x) {
+        a += partial[3 * s];
+        r += partial[3 * s + 1];
+        g += partial[3 * s + 2];
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = r;
+    red[2][threadIdx.x] = g;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double SA = red[0][0], SR = red[1][0], SG = red[2][0];
+        grad[0] = coef[0] * SA;
+        grad[1] = coef[1] * SA + coef[2] * SR + coef[3] * SG;
+        grad[2] = coef[4] * SG;
+    }
+}
+
+}  // namespace
+
+// Interleaved columns need a CTA of at least one full warp (T G >= 32).
+bool lct_gen_supported(int dtype, int log2n, int cols) {
+    if (log2n < 1 || log2n > 12) return false;
+    if (!cols) return true;
+    return dtype == 0 ? log2n >= 7 : log2n >= 8;
+}
+
+// cols: 0 = rows (signals contiguous), 1 = interleaved columns.
+cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad, const void* in,
+                           void* out, const lct_desc* desc, int desc_step, int64_t count,
+                           const void* tw, int64_t es, int64_t P, int64_t big,
+                           const void* fwd_out, const void* fwd_in, double* partial,
+                           cudaStream_t stream) {
+    if (dtype == 0) {
+        if (cols)
+            return gen_mode<float, 4>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es,
+                                      P, big, fwd_out, fwd_in, partial, stream);
+        return gen_mode<float, 1>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es, P,
+                                  big, fwd_out, fwd_in, partial, stream);
+    }
+    if (cols)
+        return gen_mode<double, 2>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es, P,
+                                   big, fwd_out, fwd_in, partial, stream);
+    return gen_mode<double, 1>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es, P, big,
+                               fwd_out, fwd_in, partial, stream);
+}
+
+cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, int coef_step,
+                                     int64_t count, int shared, double* grad, cudaStream_t stream) {
+    if (shared)
+        k_grad_finalize<<<1, 256, 0, stream>>>(partial, coef, coef_step, count, 1, grad);
+    else
+        k_grad_finalize<<<(unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096), 256, 0,
+                          stream>>>(partial, coef, coef_step, count, 0, grad);
+    return cudaGetLastError();
+}

@@ -117,6 +117,22 @@ cudaError_t lct_launch_diag_ragged(int dtype, const void* in, void* out, const l
                                    const int32_t* idx, int64_t count, int32_t* status,
                                    cudaStream_t stream);
 
+// General single-CTA kernel (k_general.cu): forward or adjoint, rows
+// (cols = 0) or interleaved columns (cols = 1), optional gradient sums
+// (SA, SR, SG) per signal into partial[3 s ..].  Signal s starts at D.offset
+// (desc_step = 1) or (s / P) * big + (s % P); element stride es.
+bool lct_gen_supported(int dtype, int log2n, int cols);
+cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad, const void* in,
+                           void* out, const lct_desc* desc, int desc_step, int64_t count,
+                           const void* tw, int64_t es, int64_t P, int64_t big,
+                           const void* fwd_out, const void* fwd_in, double* partial,
+                           cudaStream_t stream);
+// grad[3 s + {0,1,2}] = (dl/da, dl/db, dl/dd) from the sums; coef: 5 doubles
+// per signal (coef_step 1) or shared (coef_step 0); shared != 0 sums over
+// the signals into grad[0..2].
+cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, int coef_step,
+                                     int64_t count, int shared, double* grad, cudaStream_t stream);
+
 // Plain FP64 baseline pieces.  work: complex128 [count][N].
 cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,
                                  const lct_desc* desc, int desc_step, int64_t count,

@@ -48,3 +48,24 @@ def test_ragged_plan_counts_and_kinds():
     fr = kinds == W.KIND_FRFT
     zz = np.abs(r["z"][fr])
     assert (zz >= 0.3).all() and (zz <= 0.95).all()
+
+
+def test_keys_upsampling_reproduces_linear_functions():
+    """The Keys cubic (a = -0.5) reproduces polynomials up to degree 2 away
+    from the edges; rows sum to one everywhere."""
+    Wm = W.keys_upsample_matrix(256, 64)
+    assert np.allclose(Wm.sum(axis=1), 1.0, atol=1e-12)
+    src = np.arange(64, dtype=np.float64)
+    u = (np.arange(256) + 0.5) * 64 / 256 - 0.5
+    inner = (u > 2) & (u < 60)
+    assert np.allclose((Wm @ src)[inner], u[inner], atol=1e-12)
+
+
+def test_fields_batch_shape_and_envelope():
+    x = np.linspace(-10, 10, 128)
+    f, ax, ay = W.fields_batch(x, count=2)
+    assert f.shape == (2, 128, 128)
+    env = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / 72.0)
+    assert np.allclose(np.abs(f[0]), env)
+    for p in (ax, ay):
+        assert abs(p[0] * p[3] - p[1] * p[2] - 1) < 1e-12

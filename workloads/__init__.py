@@ -169,3 +169,40 @@ def ragged_signal(x: np.ndarray, s: float, q: float, rng: np.random.Generator,
     """One G1 signal on grid x (the noise drawn from rng)."""
     out = np.empty((1, len(x)), dtype=dtype)
     return g1_fill(rng, x, np.array([s]), np.array([q]), out)[0]
+
+
+# ----------------------------------------------------------------------------
+# 2-D fields: Gaussian beam times a smooth random phase screen
+# ----------------------------------------------------------------------------
+def keys_upsample_matrix(n_out: int, n_in: int, a: float = -0.5) -> np.ndarray:
+    """[n_out, n_in] bicubic (Keys kernel, parameter a) interpolation matrix,
+    half-pixel centres (align_corners=False), edge samples replicated."""
+    def kern(t):
+        t = np.abs(t)
+        return np.where(t <= 1, (a + 2) * t ** 3 - (a + 3) * t ** 2 + 1,
+                        np.where(t < 2, a * t ** 3 - 5 * a * t ** 2 + 8 * a * t - 4 * a, 0.0))
+    Wm = np.zeros((n_out, n_in))
+    for i in range(n_out):
+        u = (i + 0.5) * n_in / n_out - 0.5
+        j0 = int(np.floor(u))
+        for j in range(j0 - 1, j0 + 3):
+            Wm[i, min(max(j, 0), n_in - 1)] += kern(u - j)
+    return Wm
+
+
+def fields_batch(x: np.ndarray, count: int = 8, seed: int = SEED_FIELDS, width: float = 6.0,
+                 screen: int = 64):
+    """count complex128 fields on the grid x (x) x: exp(-(x^2+y^2)/(2 w^2)) e^{i phi},
+    phi = bicubic upsampling of a screen x screen N(0,1) array; per-axis (a,b,c,d)
+    from G1.  Returns (fields [count, n, n], abcd_x, abcd_y)."""
+    rng = rng_for(seed)
+    p = g1_params(rng, 2)
+    abcd_x, abcd_y = p[0], p[1]
+    n = len(x)
+    Wm = keys_upsample_matrix(n, screen)
+    env = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (2 * width * width))
+    out = np.empty((count, n, n), dtype=np.complex128)
+    for k in range(count):
+        phi = Wm @ rng.standard_normal((screen, screen)) @ Wm.T
+        out[k] = env * np.exp(1j * phi)
+    return out, abcd_x, abcd_y
