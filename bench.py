@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6"],
                     help="fused kernel variant (auto: the library's autotuner)")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
@@ -378,7 +378,7 @@ def main():
     achieved = n_points * BYTES_PER_POINT / (ms_per_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_per_launch(n_points),
-                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>"}[variant]
+                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>", 5: "k_xft_cluster", 6: "k_xft_pair<12, 2, 3>"}[variant]
                           + " (N=4096, complex64)",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}

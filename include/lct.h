@@ -122,7 +122,9 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     16-byte aligned signal starts; else variant 3);
  *  5  thread-block cluster of N/8192 CTAs per signal exchanging through
  *     distributed shared memory (N = 16384 .. 65536; the only kernel for
- *     N >= 32768 in complex64 and N >= 16384 in complex128).
+ *     N >= 32768 in complex64 and N >= 16384 in complex128);
+ *  6  paired with eight samples per thread (radix-8 passes), fewer
+ *     registers and more resident warps (complex64, N = 64 .. 8192).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 lct_status lct_plan_get_variant(lct_plan plan, int* variant);

@@ -16,24 +16,26 @@ namespace {
 
 using namespace xft;
 
-template <int L>
+template <int L, int LE = 4>
 struct pair_shape {
-    static constexpr int T = shape<L>::T;
+    static constexpr int T = shape<L, LE>::T;
     static constexpr int PPC = T >= 256 ? 1 : 256 / T;     // signal pairs per CTA
     static constexpr int THREADS = T * PPC;
+    static constexpr int PS = LE == 3 ? 3 : 4;              // padding shift (16-byte samples)
+    static constexpr int NP = padded_len<L, PS>();
 };
 
 __device__ __forceinline__ cpx<pf> pack(cpx<float> a, cpx<float> b) {
     return {pf_make(a.x, b.x), pf_make(a.y, b.y)};
 }
 
-template <int L, int MINB>
-__global__ void __launch_bounds__(pair_shape<L>::THREADS, MINB)
+template <int L, int MINB, int LE = 4>
+__global__ void __launch_bounds__(pair_shape<L, LE>::THREADS, MINB)
 k_xft_pair(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
            const lct_desc* __restrict__ desc, int desc_step, int64_t count,
            const cpx<pf>* __restrict__ tw) {
-    using S = shape<L>;
-    using F = pair_shape<L>;
+    using S = shape<L, LE>;
+    using F = pair_shape<L, LE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<pf>* smem = reinterpret_cast<cpx<pf>*>(smem_raw);
     const int tid = threadIdx.x;
@@ -45,7 +47,7 @@ k_xft_pair(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
     const lct_desc DB = desc[desc_step && act_b ? sa + 1 : 0];
     const int64_t base_a = desc_step ? DA.offset : sa * (int64_t)S::N;
     const int64_t base_b = desc_step ? DB.offset : (sa + 1) * (int64_t)S::N;
-    cpx<pf>* buf = smem + sl * S::NP;
+    cpx<pf>* buf = smem + sl * F::NP;
     const bool dec_a = (DA.flags & LCT_FLAG_DECAY) != 0, dec_b = (DB.flags & LCT_FLAG_DECAY) != 0;
 
     cpx<pf> v[S::E];
@@ -58,7 +60,7 @@ k_xft_pair(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
         const cpx<float> ca = pre_chirp<L>(DA, n, dec_a), cb = pre_chirp<L>(DB, n, dec_b);
         v[e] = cmul(pack(fa, fb), pack(ca, cb));
     }
-    dft_signal<L, -1>(v, buf, i, tw);
+    dft_signal<L, -1, false, LE, F::PS>(v, buf, i, tw);
     const pf sc = pf_make((float)DA.scale, (float)DB.scale);
 #pragma unroll
     for (int e = 0; e < S::E; ++e) {
@@ -190,13 +192,12 @@ cudaError_t launch_pair_tma(const void* in, void* out, const lct_desc* desc, int
     return cudaGetLastError();
 }
 
-template <int L, int MINB>
+template <int L, int MINB, int LE = 4>
 cudaError_t launch_pair(const void* in, void* out, const lct_desc* desc, int desc_step,
                         int64_t count, const void* tw, cudaStream_t stream) {
-    using S = shape<L>;
-    using F = pair_shape<L>;
-    const size_t smem = (size_t)F::PPC * S::NP * sizeof(cpx<pf>);
-    auto kern = k_xft_pair<L, MINB>;
+    using F = pair_shape<L, LE>;
+    const size_t smem = (size_t)F::PPC * F::NP * sizeof(cpx<pf>);
+    auto kern = k_xft_pair<L, MINB, LE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -227,6 +228,25 @@ cudaError_t pair_dispatch(int log2n, const void* in, void* out, const lct_desc* 
 }  // namespace
 
 bool lct_fused_pair_supported(int dtype, int log2n) { return dtype == 0 && log2n >= 5 && log2n <= 13; }
+// Eight samples per thread (radix-8 passes): half the registers of the
+// 16-sample kernel, so two CTAs of up to 512 threads stay resident at <= 64
+// registers (complex64, N = 64 .. 8192).
+bool lct_fused_pair8_supported(int dtype, int log2n) { return dtype == 0 && log2n >= 6 && log2n <= 13; }
+
+cudaError_t lct_launch_fused_pair8(int dtype, int log2n, const void* in, void* out,
+                                   const lct_desc* desc, int desc_step, int64_t count,
+                                   const void* tw_pair8, cudaStream_t stream) {
+    if (dtype != 0) return cudaErrorInvalidValue;
+    switch (log2n) {
+#define LCT_CASE(L, MB) \
+    case L: return launch_pair<L, MB, 3>(in, out, desc, desc_step, count, tw_pair8, stream);
+        LCT_CASE(6, 4) LCT_CASE(7, 4) LCT_CASE(8, 4) LCT_CASE(9, 4) LCT_CASE(10, 4)
+        LCT_CASE(11, 4) LCT_CASE(12, 2) LCT_CASE(13, 1)
+#undef LCT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // One pair per CTA needs T = N/16 >= 256 threads to keep the SM busy: N = 4096.
 bool lct_fused_pair_tma_supported(int dtype, int log2n) { return dtype == 0 && log2n == 12; }
 

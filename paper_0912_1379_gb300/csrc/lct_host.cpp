@@ -196,15 +196,17 @@ namespace {
 std::mutex g_tw_mu;
 std::map<std::tuple<int, int, int>, void*> g_tw;   // (device, dtype, log2n) -> table
 
+// Table of the Stockham engine with radix E = 2^le passes (see xft_engine.cuh).
 template <class T>
-std::vector<T> build_twiddles(int log2n) {
-    const int P = log2n >= 4 ? (log2n + 3) / 4 : 1;
-    const int R0 = 1 << (log2n - 4 * (P - 1));
+std::vector<T> build_twiddles(int log2n, int le = 4) {
+    const int E = 1 << le;
+    const int P = log2n >= le ? (log2n + le - 1) / le : 1;
+    const int R0 = 1 << (log2n - le * (P - 1));
     std::vector<T> t;
     for (int p = 1; p < P; ++p) {
-        const int64_t ns = (int64_t)R0 << (4 * (p - 1));
-        const int64_t M = 16 * ns;
-        for (int j = 1; j < 16; ++j)
+        const int64_t ns = (int64_t)R0 << (le * (p - 1));
+        const int64_t M = E * ns;
+        for (int j = 1; j < E; ++j)
             for (int64_t k = 0; k < ns; ++k) {
                 const double ang = 2.0 * M_PI * (double)((j * k) % M) / (double)M;
                 t.push_back((T)std::cos(ang));
@@ -245,15 +247,15 @@ const void* lct_twiddle_table(int dtype, int log2n) {
     return d;
 }
 
-const void* lct_twiddle_table_pair(int log2n) {
-    if (log2n < 5) return nullptr;
+const void* lct_twiddle_table_pair(int log2n, int le) {
+    if (log2n <= le) return nullptr;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> g(g_tw_mu);
-    auto key = std::make_tuple(dev, 2, log2n);
+    auto key = std::make_tuple(dev, 10 + le, log2n);
     auto it = g_tw.find(key);
     if (it != g_tw.end()) return it->second;
-    std::vector<float> t = build_twiddles<float>(log2n);
+    std::vector<float> t = build_twiddles<float>(log2n, le);
     std::vector<float> b(2 * t.size());
     for (size_t k = 0; k < t.size() / 2; ++k) {
         b[4 * k + 0] = t[2 * k];
@@ -596,6 +598,12 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
     if (!lct_fused_supported(p->dtype, log2n)) return LCT_ERR_UNSUPPORTED;
     const void* tw = lct_twiddle_table(p->dtype, log2n);
     if (log2n >= 5 && !tw) return LCT_ERR_OOM;
+    if (variant == 6 && lct_fused_pair8_supported(p->dtype, log2n)) {
+        const void* tw8 = lct_twiddle_table_pair(log2n, 3);
+        if (!tw8) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_fused_pair8(p->dtype, log2n, in, out, p->d_desc, desc_step,
+                                                batch, tw8, stream));
+    }
     if (variant == 4 && pair_tma_ok(p, in)) {
         const void* tw2 = lct_twiddle_table_pair(log2n);
         if (!tw2) return LCT_ERR_OOM;
@@ -805,7 +813,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 5) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 6) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }
@@ -824,8 +832,9 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         return LCT_OK;
     }
     const int saved = plan->variant;
-    int candidates[6] = {0, 0, 0, 0, 0, 0};
+    int candidates[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int n_cand = 1;
+    if (lct_fused_pair8_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 6;
     if (lct_cluster_local_log2(plan->dtype, plan->desc[0].log2n) >= 0 &&
         lct_fused_supported(plan->dtype, plan->desc[0].log2n))
         candidates[n_cand++] = 5;

@@ -54,9 +54,10 @@ int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D);
 // entry e^{-2 pi i j k / (16 Ns_p)}, Ns_p = R0 16^(p-1), R0 the first radix.
 // Returns nullptr on failure (and for N < 32, which needs no table).
 const void* lct_twiddle_table(int dtype, int log2n);
-// Broadcast form of the complex64 table for the paired kernel: every entry
-// (wx, wy) stored as {(wx, wx), (wy, wy)} (16 bytes).
-const void* lct_twiddle_table_pair(int log2n);
+// Broadcast form of the complex64 table for the paired kernels (radix
+// 2^le passes, le = 4 or 3): every entry (wx, wy) stored as
+// {(wx, wx), (wy, wy)} (16 bytes).
+const void* lct_twiddle_table_pair(int log2n, int le = 4);
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 // Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
@@ -97,6 +98,12 @@ cudaError_t lct_launch_fused_pair(int dtype, int log2n, const void* in, void* ou
                                   const lct_desc* desc, int desc_step, int64_t count,
                                   const void* tw_pair, cudaStream_t stream);
 bool lct_fused_pair_supported(int dtype, int log2n);
+// Paired variant with eight samples per thread (radix-8 passes), complex64,
+// N = 64 .. 8192.  tw_pair8: lct_twiddle_table_pair(log2n, 3).
+cudaError_t lct_launch_fused_pair8(int dtype, int log2n, const void* in, void* out,
+                                   const lct_desc* desc, int desc_step, int64_t count,
+                                   const void* tw_pair8, cudaStream_t stream);
+bool lct_fused_pair8_supported(int dtype, int log2n);
 
 // Persistent paired variant with bulk-async refill of its single shared
 // buffer (complex64, N = 4096, 16-byte aligned signal starts).

@@ -1,9 +1,10 @@
 // Stockham DFT engine shared by the XFT kernels.
 //
 // Self-sorting Stockham formulation of the N-point DFT (N = 2^L).  Every
-// thread owns E = 16 samples (E = N for N < 16), T = N/E threads per signal.
-// Pass p has radix R_p (first pass 2^(L mod 4) or 16, then 16) and
-// sub-length Ns_p = product of the previous radices.  In every pass thread i
+// thread owns E = 2^LE samples (LE = 4 by default, 3 for the low-register
+// kernels; E = N for smaller N), T = N/E threads per signal.  Pass p has
+// radix R_p (first pass 2^(L mod LE) or E, then E) and sub-length
+// Ns_p = product of the previous radices.  In every pass thread i
 // holds the samples i + e T (e = 0..E-1) -- the coalesced pattern, so the
 // first pass can read global memory directly and the last pass can write it
 // directly -- multiplies sample j of its group by the twiddle
@@ -13,33 +14,40 @@
 // by one slot per 16 samples, which makes every exchange free of bank
 // conflicts (for T >= 16).
 //
-// Twiddles come from a per-N table laid out [pass][j-1][k] (see
+// Twiddles come from a per-(N, E) table laid out [pass][j-1][k] (see
 // lct_twiddle_table), so that the 32 lanes of a warp read 32 consecutive
-// entries.  Entry (p, j, k) = e^{-2 pi i j k / (16 Ns_p)}; the inverse
-// transform (S = +1) uses the conjugate.
+// entries.  Entry (p, j, k) = e^{-2 pi i j k / (E Ns_p)}; the inverse
+// transform (S = +1) uses the conjugate.  Offset of pass p:
+// sum_{q<p} (E-1) Ns_q = Ns_p - R_0.
 #pragma once
 #include "xft_common.cuh"
 
 namespace xft {
 
-constexpr int pass_count(int L) { return L >= 4 ? (L + 3) / 4 : 1; }
-constexpr int first_radix(int L) { return 1 << (L - 4 * (pass_count(L) - 1)); }
-__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+constexpr int pass_count(int L, int LE = 4) { return L >= LE ? (L + LE - 1) / LE : 1; }
+constexpr int first_radix(int L, int LE = 4) { return 1 << (L - LE * (pass_count(L, LE) - 1)); }
+// Shared-memory padding: one slot every 2^PS samples (PS = 4 makes the
+// exchanges of 8-byte samples with E = 16 conflict-free; PS = 3 those of
+// 16-byte samples with E = 8).
+template <int PS = 4>
+__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> PS); }
+template <int L, int PS = 4>
+constexpr int padded_len() { return (1 << L) + ((1 << L) >> PS); }
 
-template <int L>
+template <int L, int LE = 4>
 struct shape {
     static constexpr int N = 1 << L;
-    static constexpr int E = L >= 4 ? 16 : N;
+    static constexpr int E = L >= LE ? (1 << LE) : N;
     static constexpr int T = N / E;
-    static constexpr int P = pass_count(L);
+    static constexpr int P = pass_count(L, LE);
     static constexpr int NP = N + (N >> 4);
 };
 
-template <int L, int p>
+template <int L, int p, int LE = 4>
 struct pass {
-    static constexpr int RADIX = p == 0 ? first_radix(L) : 16;
-    static constexpr int NS = p == 0 ? 1 : first_radix(L) << (4 * (p - 1));
-    static constexpr int TW_OFF = NS - first_radix(L);   // sum of (16-1) Ns_q over q < p
+    static constexpr int RADIX = p == 0 ? first_radix(L, LE) : (1 << LE);
+    static constexpr int NS = p == 0 ? 1 : first_radix(L, LE) << (LE * (p - 1));
+    static constexpr int TW_OFF = NS - first_radix(L, LE);   // sum of (E-1) Ns_q over q < p
 };
 
 template <class R>
@@ -74,10 +82,10 @@ __device__ __forceinline__ cpx<R> twiddle_exact(int k, int M) {
 // Twiddles + radix-R DFTs of pass p on the registers of thread i.
 // TWC = false: twiddles read from the table; TWC = true: computed (one
 // sincospi for w = e^{S 2 pi i k/(Ns R)}, then powers by a product tree).
-template <int L, int p, int SGN, bool TWC, class R>
+template <int L, int p, int SGN, bool TWC, int LE = 4, class R>
 __device__ __forceinline__ void butterflies(cpx<R>* v, int i, const cpx<R>* __restrict__ tw) {
-    using S = shape<L>;
-    using PI = pass<L, p>;
+    using S = shape<L, LE>;
+    using PI = pass<L, p, LE>;
     constexpr int RADIX = PI::RADIX, NS = PI::NS, V = S::E / RADIX;
 #pragma unroll
     for (int vv = 0; vv < V; ++vv) {
@@ -107,10 +115,10 @@ __device__ __forceinline__ void butterflies(cpx<R>* v, int i, const cpx<R>* __re
     }
 }
 
-template <int L, int p, class R>
+template <int L, int p, int LE = 4, int PS = 4, class R>
 __device__ __forceinline__ void smem_store(const cpx<R>* v, cpx<R>* buf, int i) {
-    using S = shape<L>;
-    using PI = pass<L, p>;
+    using S = shape<L, LE>;
+    using PI = pass<L, p, LE>;
     constexpr int RADIX = PI::RADIX, NS = PI::NS, V = S::E / RADIX;
 #pragma unroll
     for (int vv = 0; vv < V; ++vv) {
@@ -118,42 +126,43 @@ __device__ __forceinline__ void smem_store(const cpx<R>* v, cpx<R>* buf, int i) 
         const int k = ip & (NS - 1);
         const int base = (ip - k) * RADIX + k;
 #pragma unroll
-        for (int j = 0; j < RADIX; ++j) buf[pad_idx(base + j * NS)] = v[vv + j * V];
+        for (int j = 0; j < RADIX; ++j) buf[pad_idx<PS>(base + j * NS)] = v[vv + j * V];
     }
 }
 
-template <int L, class R>
+template <int L, int LE = 4, int PS = 4, class R>
 __device__ __forceinline__ void smem_load(cpx<R>* v, const cpx<R>* buf, int i) {
-    using S = shape<L>;
+    using S = shape<L, LE>;
 #pragma unroll
-    for (int e = 0; e < S::E; ++e) v[e] = buf[pad_idx(i + e * S::T)];
+    for (int e = 0; e < S::E; ++e) v[e] = buf[pad_idx<PS>(i + e * S::T)];
 }
 
 // Passes p..P-1, the first of which reads the shared-memory output of pass p-1.
-template <int L, int p, int SGN, bool TWC, class R>
+template <int L, int p, int SGN, bool TWC, class R, int LE, int PS,
+          bool DONE = (p >= shape<L, LE>::P)>
 struct passes_from {
     __device__ __forceinline__ static void run(cpx<R>* v, cpx<R>* buf, int i,
                                                const cpx<R>* __restrict__ tw) {
         if (p > 1) __syncthreads();          // previous exchange fully read
-        smem_store<L, p - 1>(v, buf, i);
+        smem_store<L, p - 1, LE, PS>(v, buf, i);
         __syncthreads();
-        smem_load<L>(v, buf, i);
-        butterflies<L, p, SGN, TWC>(v, i, tw);
-        passes_from<L, p + 1, SGN, TWC, R>::run(v, buf, i, tw);
+        smem_load<L, LE, PS>(v, buf, i);
+        butterflies<L, p, SGN, TWC, LE>(v, i, tw);
+        passes_from<L, p + 1, SGN, TWC, R, LE, PS>::run(v, buf, i, tw);
     }
 };
-template <int L, int SGN, bool TWC, class R>
-struct passes_from<L, shape<L>::P, SGN, TWC, R> {
+template <int L, int p, int SGN, bool TWC, class R, int LE, int PS>
+struct passes_from<L, p, SGN, TWC, R, LE, PS, true> {
     __device__ __forceinline__ static void run(cpx<R>*, cpx<R>*, int, const cpx<R>* __restrict__) {}
 };
 
 // Whole DFT on the registers v (thread i holds samples i + e T on entry and
 // output samples i + e T on exit).  buf: this signal's padded shared buffer.
-template <int L, int SGN, bool TWC = false, class R>
+template <int L, int SGN, bool TWC = false, int LE = 4, int PS = 4, class R>
 __device__ __forceinline__ void dft_signal(cpx<R>* v, cpx<R>* buf, int i,
                                            const cpx<R>* __restrict__ tw) {
-    butterflies<L, 0, SGN, TWC>(v, i, tw);
-    passes_from<L, 1, SGN, TWC, R>::run(v, buf, i, tw);
+    butterflies<L, 0, SGN, TWC, LE>(v, i, tw);
+    passes_from<L, 1, SGN, TWC, R, LE, PS>::run(v, buf, i, tw);
 }
 
 // Streaming global load that does not allocate in L1 (keeps the twiddle
