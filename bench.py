@@ -40,10 +40,32 @@ METRIC = "LCT points/s at N=4096 batched vs plain FP64 GPU path at <=1e-5 rel er
 N_DEFAULT, COUNT_DEFAULT = 4096, 16384
 BYTES_PER_POINT = 16          # complex64: 8 B read + 8 B written
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/k_fused_pair.cu",
-                  "paper_0912_1379_gb300/csrc/xft_common.cuh", "paper_0912_1379_gb300/csrc/xft_engine.cuh",
+COMMON_SOURCES = ["paper_0912_1379_gb300/csrc/xft_common.cuh", "paper_0912_1379_gb300/csrc/xft_engine.cuh",
                   "paper_0912_1379_gb300/csrc/xft_chirp.cuh", "paper_0912_1379_gb300/csrc/xft_async.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_xft_fused_f32_n4096.json")
+KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/k_fused_pair.cu"] + COMMON_SOURCES
+SPLIT_SOURCES = ["paper_0912_1379_gb300/csrc/k_split.cu"] + COMMON_SOURCES
+# ncu DRAM-traffic summaries, one per kernel: (file, sources whose hash it records)
+TRAFFIC_FILES = {
+    "k_xft_fused<12, float>": ("traffic_xft_fused_f32_n4096.json", KERNEL_SOURCES),
+    "k_xft_split<12, bf16, 3 products>": ("traffic_xft_split_bf16_n4096.json", SPLIT_SOURCES),
+    "k_xft_split<12, fp16, 3 products>": ("traffic_xft_split_fp16_n4096.json", SPLIT_SOURCES),
+    "k_xft_split<12, fp16, 1 product>": ("traffic_xft_split_fp16x1_n4096.json", SPLIT_SOURCES),
+}
+
+
+PRECISIONS = {"native": 0, "split_bf16": 1, "split_fp16": 2, "fp16": 3}
+DTYPES = {"native": "f32", "split_bf16": "bf16 hi+lo operands, f32 accumulate",
+          "split_fp16": "f16 hi+lo operands, f32 accumulate", "fp16": "f16 operands, f32 accumulate"}
+VARIANT_KERNELS = {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>",
+                   2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>",
+                   5: "k_xft_cluster", 6: "k_xft_pair<12, 2, 3>"}
+SPLIT_KERNELS = {"split_bf16": "k_xft_split<12, bf16, 3 products>",
+                 "split_fp16": "k_xft_split<12, fp16, 3 products>",
+                 "fp16": "k_xft_split<12, fp16, 1 product>"}
+
+
+def kernel_name(variant, precision):
+    return VARIANT_KERNELS[variant] if variant is not None else SPLIT_KERNELS[precision]
 
 
 def parse():
@@ -60,6 +82,10 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
     ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6"],
                     help="fused kernel variant (auto: the library's autotuner)")
+    ap.add_argument("--precision", default="native",
+                    choices=["native", "split_bf16", "split_fp16", "fp16"],
+                    help="native: FP32 fused kernel (headline); split_*/fp16: the DFT passes "
+                         "on the tensor cores")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
                          "instances in one graph launch")
@@ -73,9 +99,9 @@ def dist_env():
     return rank, world, local
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in (KERNEL_SOURCES if sources is None else sources):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -91,15 +117,19 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(n_points: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None), scaled to this launch size."""
+def traffic_per_launch(n_points: int, kernel: str):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if
+    it was taken on the current kernel source (else None), scaled to this
+    launch size."""
+    if kernel not in TRAFFIC_FILES:
+        return None
+    fname, sources = TRAFFIC_FILES[kernel]
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(os.path.join(ROOT, "profiles", fname)) as fh:
             j = json.load(fh)
     except Exception:
         return None
-    if j.get("kernel_hash") != kernel_hash():
+    if j.get("kernel_hash") != kernel_hash(sources) or j.get("kernel") != kernel:
         return None
     per_point = float(j["dram_bytes"]) / float(j["points"])
     return per_point * n_points
@@ -176,15 +206,16 @@ def cpu_oracle_rate(x, params, f, min_seconds: float = 10.0, max_signals: int = 
     O.build()
     done, t0 = 0, time.perf_counter()
     chunk = 8
+    outs = []
     while done < max_signals:
         s = slice(done, done + chunk)
-        O.lct(f[s].astype(np.complex128), params[s])
+        outs.append(O.lct(f[s].astype(np.complex128), params[s]))
         done += f[s].shape[0]
         if time.perf_counter() - t0 >= min_seconds or done >= f.shape[0]:
             break
     dt = time.perf_counter() - t0
     N = f.shape[1]
-    return done * N / dt, done, dt, O.num_threads()
+    return done * N / dt, done, dt, O.num_threads(), np.concatenate(outs)
 
 
 def reference_arm(args, rank, world):
@@ -318,6 +349,7 @@ def main():
     x = lct.lct_input_grid(N)
     params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)
     plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+    prec_code = PRECISIONS[args.precision]
     h_in = torch.from_numpy(f).pin_memory()
     d_in = h_in.cuda()
     d_out = torch.empty_like(d_in)
@@ -327,7 +359,10 @@ def main():
     def step():
         plan.execute(d_in, d_out, count, stream)
 
-    if args.variant == "auto":
+    if prec_code != lct.LCT_PREC_NATIVE:
+        variant = None
+        plan.set_precision(prec_code)
+    elif args.variant == "auto":
         variant = plan.autotune(d_in, d_out, count, stream)
     else:
         variant = int(args.variant)
@@ -377,9 +412,9 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = n_points * BYTES_PER_POINT / (ms_per_step * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(n_points),
-                "kernel": {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>", 2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>", 5: "k_xft_cluster", 6: "k_xft_pair<12, 2, 3>"}[variant]
-                          + " (N=4096, complex64)",
+                "frac": achieved / peak,
+                "traffic": traffic_per_launch(n_points, kernel_name(variant, args.precision)),
+                "kernel": kernel_name(variant, args.precision) + " (N=4096, complex64)",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}
 
@@ -399,12 +434,14 @@ def main():
         pms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
         plain = {"value": world * n_points / (pms * 1e-3), "unit": "points/s", "ms_per_step": pms,
                  "path": "chirp kernel + cuFFT Z2Z + chirp kernel, FP64 workspace"}
-        plan.set_precision(lct.LCT_PREC_NATIVE)
         torch.cuda.synchronize()
         # release the plain path's workspace
         plan.destroy()
         plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
-        plan.set_variant(variant)
+        if variant is None:
+            plan.set_precision(prec_code)
+        else:
+            plan.set_variant(variant)
         step()
         torch.cuda.synchronize()
 
@@ -435,25 +472,33 @@ def main():
                "api": "lct_execute on device buffers with pinned-host copies on the same stream"}
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu:
-        rate, nsig, dt, cores = cpu_oracle_rate(x, params, f)
+        torch.cuda.synchronize()
+        rate, nsig, dt, cores, ref = cpu_oracle_rate(x, params, f)
         cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
                "sample": "first %d signals of the %d x N=%d workload, %.1f s" % (nsig, count, N, dt)}
+        got = d_out[:nsig].cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        accuracy = {"rel_l2_max": float(err.max()), "rel_l2_median": float(np.median(err)),
+                    "signals": int(nsig), "against": "FP64 oracle on the cpu_baseline sample"}
 
     plan.destroy()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": "uniform batch %d x N=%d complex64, G1 per-signal (a,b,c,d), seed %d"
                                    % (count, N, W.SEED_UNIFORM_4096),
                        "signals_per_gpu": count, "N": N, "transforms_per_s": value / N,
-                       "kernel_variant": variant,
+                       "precision": args.precision, "kernel_variant": variant,
                        "l2": "inputs larger than L2 (512 MiB per buffer), no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

@@ -61,7 +61,17 @@ typedef enum { LCT_C64 = 0, LCT_C128 = 1 } lct_dtype;
  *  PLAIN64     unfused FP64 baseline: a chirp kernel, a library FFT (cuFFT
  *              Z2Z, forward sign) on an FP64 workspace, a chirp+scale kernel.
  *  SPLIT_BF16, SPLIT_FP16, FP16
- *              reserved for the tensor-core DFT; LCT_ERR_UNSUPPORTED until built.
+ *              tensor-core DFT (complex64 plans, one N in [16, 4096]): the
+ *              radix-16 DFT passes run as real 32x32 DFT-matrix products
+ *              (mma m16n8k16, FP32 accumulation); chirps and twiddles in FP32
+ *              with the exact phases below.  SPLIT_*: operands split into
+ *              hi + lo halves (BF16 or FP16), three products hi.hi + hi.lo +
+ *              lo.hi; SPLIT_FP16 and FP16 scale each signal by a power of two
+ *              so that the FP16 range holds.  FP16: one product of FP16
+ *              operands (relative L2 error about 1e-3).  lct_plan_set_precision
+ *              returns LCT_ERR_UNSUPPORTED for complex128 plans, ragged plans
+ *              and other N.  b = 0 plans have no DFT and ignore the choice.
+ *              lct_backward and the 2-D transform use NATIVE only.
  * Phases: every chirp phase is a turn fraction held as a fixed-point integer
  * (64 bits of fraction for FP32 paths, 128 for FP64 paths) and multiplied by
  * the integer m^2 (m = 2k - N + 1) with wrap-around, so no phase loses

@@ -320,6 +320,10 @@ struct lct_plan_s {
     double* d_coef = nullptr;
     double* d_partial = nullptr;
     int64_t partial_count = 0;
+    // offset properties, fixed at creation: every offset even (16-byte signal
+    // starts when `in` is 16-byte aligned) and offset[s] == s N0
+    bool even_offsets = true;
+    bool contiguous = true;
 };
 
 // ---------------------------------------------------------------------------
@@ -496,6 +500,8 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
         lct_status st = make_desc(N[s], abcd + 8 * s, offsets ? offsets[s] : 0, &p->desc[s]);
         if (st != LCT_OK) { delete p; return st; }
         if (N[s] != p->N0) p->N0 = 0;
+        if (p->desc[s].offset % 2) p->even_offsets = false;
+        if (p->desc[s].offset != s * N[0]) p->contiguous = false;
     }
     bool mixed_kind = false;
     for (int64_t s = 1; s < count; ++s)
@@ -558,11 +564,7 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
 
 // Can a bulk-async variant run this plan on `in` (16-byte aligned starts)?
 bool tma_aligned(lct_plan p, const void* in) {
-    if (((uintptr_t)in) % 16) return false;
-    if (p->is_batch)
-        for (const lct_desc& D : p->desc)
-            if (D.offset % 2) return false;
-    return true;
+    return ((uintptr_t)in) % 16 == 0 && (!p->is_batch || p->even_offsets);
 }
 
 bool pair_tma_ok(lct_plan p, const void* in) {
@@ -571,12 +573,7 @@ bool pair_tma_ok(lct_plan p, const void* in) {
 
 // Can variant 1 (persistent, bulk-async prefetch) run this plan on `in`?
 bool tma_ok(lct_plan p, const void* in) {
-    if (!lct_fused_tma_supported(p->dtype, p->desc[0].log2n)) return false;
-    if (((uintptr_t)in) % 16) return false;
-    if (p->is_batch)
-        for (const lct_desc& D : p->desc)
-            if (D.offset % 2) return false;
-    return true;
+    return lct_fused_tma_supported(p->dtype, p->desc[0].log2n) && tma_aligned(p, in);
 }
 
 int effective_variant(lct_plan p) {
@@ -805,8 +802,16 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
             return LCT_OK;
         case LCT_PREC_SPLIT_BF16:
         case LCT_PREC_SPLIT_FP16:
-        case LCT_PREC_FP16:
-            return LCT_ERR_UNSUPPORTED;
+        case LCT_PREC_FP16: {
+            // tensor-core DFT: complex64, one N in [16, 4096] (b = 0 plans have
+            // no DFT and run their diagonal kernel whatever the precision)
+            if (plan->dtype != LCT_C64 || plan->ragged || plan->N0 == 0) return LCT_ERR_UNSUPPORTED;
+            const int log2n = ilog2_exact(plan->N0);
+            if (plan->desc[0].kind == LCT_KIND_XFT && !lct_split_supported(plan->dtype, log2n))
+                return LCT_ERR_UNSUPPORTED;
+            plan->prec = precision;
+            return LCT_OK;
+        }
         default:
             return LCT_ERR_ARG;
     }
@@ -911,6 +916,14 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                 if (plan->desc[s].offset != s * plan->N0) return LCT_ERR_UNSUPPORTED;
         }
         return run_plain(plan, in, out, batch, desc_step, stream);
+    }
+    if (plan->prec == LCT_PREC_SPLIT_BF16 || plan->prec == LCT_PREC_SPLIT_FP16 ||
+        plan->prec == LCT_PREC_FP16) {
+        const void* tw = lct_twiddle_table(plan->dtype, log2n);
+        if (log2n >= 5 && !tw) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_split((int)plan->prec, log2n, in, out, plan->d_desc,
+                                          desc_step, batch, tw, tma_aligned(plan, in) ? 1 : 0,
+                                          plan->contiguous ? 1 : 0, plan->d_status, stream));
     }
     return run_fused(plan, in, out, batch, desc_step, effective_variant(plan), stream);
 }

@@ -112,6 +112,19 @@ cudaError_t lct_launch_fused_pair_tma(int dtype, int log2n, const void* in, void
                                       const void* tw_pair, int32_t* status, cudaStream_t stream);
 bool lct_fused_pair_tma_supported(int dtype, int log2n);
 
+// Split-precision XFT on the tensor cores (complex64, N = 16 .. 4096; a CTA
+// transforms 4096/N signals).  mode: 1 = split BF16 (three products),
+// 2 = split FP16 (three products, per-signal power-of-two scaling), 3 = FP16
+// (one product).  tw: lct_twiddle_table(0, log2n) (unused for N = 16).
+// async_ok: every signal start is 16-byte aligned, so inputs may arrive by
+// bulk-async copies (a timed-out wait records LCT_DEV_TIMEOUT in *status);
+// contiguous: signal s of the launch starts at element s N of `in` (one
+// copy per tile).
+cudaError_t lct_launch_split(int mode, int log2n, const void* in, void* out, const lct_desc* desc,
+                             int desc_step, int64_t count, const void* tw, int async_ok,
+                             int contiguous, int32_t* status, cudaStream_t stream);
+bool lct_split_supported(int dtype, int log2n);
+
 // Diagonal branch (b == 0) for `count` signals of N = 2^log2n; idx as for
 // lct_launch_fused (may be null).
 cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,

@@ -104,6 +104,39 @@ def test_variant_selection_host_only():
         lct.lct_plan_destroy(p)
 
 
+def test_precision_selection_host_only():
+    """Tensor-core precisions: complex64, one N in [16, 4096]; b = 0 plans
+    (no DFT) accept them at any N; complex128 and ragged plans do not."""
+    split = (lct.LCT_PREC_SPLIT_BF16, lct.LCT_PREC_SPLIT_FP16, lct.LCT_PREC_FP16)
+
+    def status(N, abcd, dtype=lct.LCT_C64, prec=lct.LCT_PREC_SPLIT_BF16):
+        p = lct.lct_plan_create(N, *abcd, dtype=dtype)
+        try:
+            lct.lct_plan_set_precision(p, prec)
+            return 0
+        except lct.LctError as e:
+            return e.status
+        finally:
+            lct.lct_plan_destroy(p)
+
+    gen = (1.0, 2.0, 0.5, 2.0)
+    for prec in split:
+        for N in (16, 32, 256, 2048, 4096):
+            assert status(N, gen, prec=prec) == 0
+        for N in (2, 8, 8192, 65536):
+            assert status(N, gen, prec=prec) == 10
+        assert status(1024, gen, dtype=lct.LCT_C128, prec=prec) == 10
+        assert status(65536, (0.5, 0.0, 1.0, 2.0), prec=prec) == 0      # b = 0: diagonal
+    assert status(1024, gen, prec=99) == 1
+    rag = lct.Plan.batch([64, 128], np.array([gen, gen]), [0, 64], dtype=lct.LCT_C64)
+    try:
+        with pytest.raises(lct.LctError) as e:
+            rag.set_precision(lct.LCT_PREC_SPLIT_FP16)
+        assert e.value.status == 10
+    finally:
+        rag.destroy()
+
+
 @pytest.mark.parametrize("z", [0.0, 1.5, 2j, complex(float("nan"), 0)])
 def test_frft_bad_z(z):
     with pytest.raises(lct.LctError) as e:
