@@ -86,9 +86,11 @@ def parse():
                     choices=["native", "split_bf16", "split_fp16", "fp16"],
                     help="native: FP32 fused kernel (headline); split_*/fp16: the DFT passes "
                          "on the tensor cores")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged", "fields2d", "backward"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
-                         "instances in one graph launch")
+                         "instances in one graph launch; fields2d: separable 2-D LCT forward + "
+                         "backward on 8 fields of 2048 x 2048; backward: lct_backward (adjoint "
+                         "+ per-signal parameter gradients) on the 16384 x N=4096 batch")
     return ap.parse_args()
 
 
@@ -313,6 +315,145 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
 
 
 # ---------------------------------------------------------------------------
+# 2-D fields: forward + backward (input gradient and (a, b, d) per axis)
+# ---------------------------------------------------------------------------
+def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+    """8 complex64 fields of 2048 x 2048 (Gaussian beam x bicubic phase
+    screen).  One step = lct2d_execute (rows, then columns) + lct2d_backward
+    (columns, then rows, each with the parameter-gradient sums) for a fixed
+    upstream gradient dl/dG of the intensity loss sum (|G|^2 - I)^2."""
+    B, n = 8, 2048
+    x = lct.lct_input_grid(n)
+    fields, ax, ay = W.fields_batch(x, B, seed=W.SEED_FIELDS + rank)
+    plan = lct.lct2d_plan_create(n, n, ay, ax, lct.LCT_C64)
+    stream = torch.cuda.current_stream()
+    xf = torch.from_numpy(fields.astype(np.complex64)).cuda()
+    mid, out = torch.empty_like(xf), torch.empty_like(xf)
+    gmid, gin = torch.empty_like(xf), torch.empty_like(xf)
+    gp = torch.zeros(6, dtype=torch.float64, device="cuda")
+    lct.lct2d_execute(plan, xf, mid, out, B, stream)
+    target = (out.abs() ** 2).roll(shifts=(7, -5), dims=(1, 2))      # a shifted intensity
+    g = (2 * (out.abs() ** 2 - target) * 2 * out).contiguous()       # dl/dG*, fixed
+    torch.cuda.synchronize()
+
+    def fwd():
+        lct.lct2d_execute(plan, xf, mid, out, B, stream)
+
+    def bwd():
+        lct.lct2d_backward(plan, g, xf, mid, out, gmid, gin, gp, B, stream)
+
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        fwd()
+        ev[2 * k + 1].record(stream)
+        bwd()
+        ev[2 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    f_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)) / args.steps
+    b_ms = sum(ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps)) / args.steps
+    f_ms, b_ms = max_over_ranks(f_ms), max_over_ranks(b_ms)
+    ms = f_ms + b_ms
+    lct.lct2d_plan_destroy(plan)
+    pts = B * n * n
+    peak, peak_kind = measured_peak()
+    fwd_bytes, bwd_bytes = 32 * pts, 64 * pts     # see the docstring of the phases below
+    phases = {
+        "forward": {"ms": f_ms, "kernels": "k_xft_fused<11, float> rows + k_xft_gen<11> columns",
+                    "algorithmic_bytes": fwd_bytes, "achieved_gbs": fwd_bytes / (f_ms * 1e-3) / 1e9},
+        "backward": {"ms": b_ms, "kernels": "k_xft_gen<11> adjoint+gradient columns, then rows; "
+                                            "two gradient finalize kernels",
+                     "algorithmic_bytes": bwd_bytes, "achieved_gbs": bwd_bytes / (b_ms * 1e-3) / 1e9},
+    }
+    achieved = bwd_bytes / (b_ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "2-D LCT forward + backward points/s (8 x 2048 x 2048 complex64)",
+            "value": world * pts / (ms * 1e-3), "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "fields2d: 8 fields 2048 x 2048, Gaussian beam x bicubic 64x64 "
+                                   "phase screen, G1 (a,b,c,d) per axis, seed %d" % W.SEED_FIELDS,
+                       "points": pts,
+                       "l2": "inputs larger than L2 (256 MiB per buffer), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "backward phase (two k_xft_gen launches: reads g, G, f, "
+                                   "writes h, 32 B/pt each)"},
+            "phases": phases,
+            "gpu_launches": 6 * args.steps,
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# 1-D backward on the headline batch
+# ---------------------------------------------------------------------------
+def backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+    """One step = lct_backward of the 16384 x 4096 batch plan: grad_in =
+    L^H g and (dl/da, dl/db, dl/dd) per signal (the adjoint kernel with the
+    gradient sums reads g, f and G and writes grad_in: 32 B/point)."""
+    N, count = args.n, args.count
+    x = lct.lct_input_grid(N)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)
+    plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(f).cuda()
+    d_out = torch.empty_like(d_in)
+    plan.execute(d_in, d_out, count, stream)
+    g = torch.randn(d_in.shape, dtype=torch.complex64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(7))
+    gin = torch.empty_like(d_in)
+    gp = torch.zeros(3 * count, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, grad_abd, bpp in [("with_param_grads", gp, 32), ("adjoint_only", None, 16)]:
+        def step():
+            lct.lct_backward(plan.handle, g, d_in, d_out, gin, grad_abd, count, stream)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        res[name] = {"ms": ms, "algorithmic_bytes": bpp * count * N,
+                     "achieved_gbs": bpp * count * N / (ms * 1e-3) / 1e9}
+    plan.destroy()
+    peak, peak_kind = measured_peak()
+    main = res["with_param_grads"]
+    if rank == 0:
+        print(json.dumps({
+            "metric": "LCT backward points/s (adjoint + parameter gradients), 16384 x N=4096",
+            "value": world * count * N / (main["ms"] * 1e-3), "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "backward: uniform batch %d x N=%d complex64, G1 per-signal "
+                                   "(a,b,c,d), seed %d; g ~ CN(0,1)" % (count, N, W.SEED_UNIFORM_4096),
+                       "l2": "inputs larger than L2 (512 MiB per buffer), no flush"},
+            "roofline": {"bound": "hbm", "achieved": main["achieved_gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": main["achieved_gbs"] / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "kernel": "k_xft_gen<12, float, adjoint, gradient sums> (+ finalize)"},
+            "phases": res,
+            "gpu_launches": 2 * args.steps,
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -345,6 +486,10 @@ def main():
 
     if args.workload == "ragged":
         return ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
+    if args.workload == "fields2d":
+        return fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
+    if args.workload == "backward":
+        return backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
     N, count = args.n, args.count
     x = lct.lct_input_grid(N)
     params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)

@@ -6,7 +6,8 @@
 //   n = c + C n2 (c < C), k = k2 + M k1 (k1 < C)
 //   X[k2 + M k1] = sum_c W_C^{c k1} W_N^{c k2} [ sum_{n2} x[c + C n2] W_M^{n2 k2} ]
 // 1. CTA r loads the contiguous chunk [r M, (r+1) M) with the pre-chirp and
-//    scatters sample n to CTA n mod C, position n div C (DSMEM stores).
+//    scatters sample n to CTA n mod C, position n div C (DSMEM stores; each
+//    thread reads runs of C consecutive samples, one for every CTA).
 // 2. Each CTA c runs the M-point Stockham DFT (xft_engine.cuh) of its
 //    stride-C subsequence and multiplies by W_N^{c k2}.
 // 3. CTA d takes k2 in [d M/C, (d+1) M/C): gathers the C values Z_c[k2],
@@ -36,8 +37,10 @@ __device__ __forceinline__ cpx<R> post_n(const lct_desc& D, int n) {
     else return post_chirp64<LN>(D, n);
 }
 
+// Input load of one sample of a run of consecutive samples read by one
+// thread: L1-allocating, so the run's neighbours come from the same lines.
 template <class R>
-__device__ __forceinline__ cpx<R> ld_in(const cpx<R>* p) { return ld_stream(p); }
+__device__ __forceinline__ cpx<R> ld_run(const cpx<R>* p) { return *p; }
 
 // Resident CTAs per SM: 4 x 256 threads (complex64, 4096-point rows),
 // 1 x 512 threads (complex128, 8192-point rows).
@@ -70,14 +73,26 @@ k_xft_cluster(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     const int64_t base = desc_step ? D.offset : sig * (int64_t)N;
     const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
 
-    // 1. contiguous chunk c, pre-chirped, scattered into stride-C subsequences
+    // 1. contiguous chunk c, pre-chirped, scattered into stride-C subsequences:
+    //    thread i takes the runs of C consecutive samples n0 + j (n0 = c M +
+    //    C (i + q T)) and writes sample j to CTA j at position n0 / C, so each
+    //    remote store instruction covers consecutive positions of one CTA.
 #pragma unroll
-    for (int e = 0; e < S::E; ++e) {
-        const int n = c * M + i + e * S::T;
-        cpx<R> f = {R(0), R(0)};
-        if (active) f = ld_in(in + base + n);
-        cpx<R>* rb = cl.map_shared_rank(buf, n & (C - 1));
-        rb[n >> LC] = cmul(f, pre_n<LN, R>(D, n, decay));
+    for (int q = 0; q < Q; ++q) {
+        const int pos = c * (M / C) + i + q * S::T;        // n0 / C
+        const int n0 = pos * C;
+        cpx<R> f[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) f[j] = {R(0), R(0)};
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) f[j] = ld_run(in + base + n0 + j);
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            cpx<R>* rb = cl.map_shared_rank(buf, j);
+            rb[pos] = cmul(f[j], pre_n<LN, R>(D, n0 + j, decay));
+        }
     }
     cl.sync();
 

@@ -198,8 +198,8 @@ cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc
     using S = shape<L>;
     using F = gen_shape<L, G>;
     size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
-    if (GRAD && smem < (size_t)F::THREADS / 32 * 4 * 3 * sizeof(double) + 64)
-        smem = (size_t)F::THREADS / 32 * 4 * 3 * sizeof(double) + 64;
+    constexpr size_t red_bytes = (size_t)F::THREADS / 32 * (G > 1 ? G : 1) * 3 * sizeof(double) + 64;
+    if (GRAD && smem < red_bytes) smem = red_bytes;
     auto kern = k_xft_gen<L, R, G, ADJ, GRAD>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -248,6 +248,8 @@ cudaError_t gen_mode(int log2n, bool adj, bool grad, const void* in, void* out,
 // dl/da, dl/db, dl/dd from the sums (SA, SR, SG); coef: per signal
 // (cA_a, cA_b, cR_b, cG_b, cG_d).  shared != 0: one parameter set for all
 // signals, the sums are added first and grad has 3 entries.
+constexpr int kFinalizeThreads = 1024;
+
 __global__ void k_grad_finalize(const double* __restrict__ partial, const double* __restrict__ coef,
                                 int coef_step, int64_t count, int shared, double* __restrict__ grad) {
     if (!shared) {
@@ -261,16 +263,28 @@ __global__ void k_grad_finalize(const double* __restrict__ partial, const double
         }
         return;
     }
-    __shared__ double red[3][256];
-    double a = 0, r = 0, g = 0;
-    for (int64_t s = threadIdx.x; s < count; s += blockDim.x) {
-        a += partial[3 * s];
-        r += partial[3 * s + 1];
-        g += partial[3 * s + 2];
+    // one CTA of kFinalizeThreads threads, four independent accumulation
+    // chains per thread, then a tree over the CTA (fixed order: deterministic)
+    __shared__ double red[3][kFinalizeThreads];
+    double a[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
+    int64_t s = threadIdx.x;
+    for (; s + 3 * (int64_t)blockDim.x < count; s += 4 * (int64_t)blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = s + u * (int64_t)blockDim.x;
+            a[u] += partial[3 * t];
+            r[u] += partial[3 * t + 1];
+            g[u] += partial[3 * t + 2];
+        }
     }
-    red[0][threadIdx.x] = a;
-    red[1][threadIdx.x] = r;
-    red[2][threadIdx.x] = g;
+    for (; s < count; s += blockDim.x) {
+        a[0] += partial[3 * s];
+        r[0] += partial[3 * s + 1];
+        g[0] += partial[3 * s + 2];
+    }
+    red[0][threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+    red[1][threadIdx.x] = (r[0] + r[1]) + (r[2] + r[3]);
+    red[2][threadIdx.x] = (g[0] + g[1]) + (g[2] + g[3]);
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if ((int)threadIdx.x < h)
@@ -317,7 +331,7 @@ cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad
 cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, int coef_step,
                                      int64_t count, int shared, double* grad, cudaStream_t stream) {
     if (shared)
-        k_grad_finalize<<<1, 256, 0, stream>>>(partial, coef, coef_step, count, 1, grad);
+        k_grad_finalize<<<1, kFinalizeThreads, 0, stream>>>(partial, coef, coef_step, count, 1, grad);
     else
         k_grad_finalize<<<(unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096), 256, 0,
                           stream>>>(partial, coef, coef_step, count, 0, grad);
