@@ -297,13 +297,15 @@ struct lct_plan_s {
     int32_t* d_status = nullptr;
     void* d_work = nullptr;
     size_t work_bytes = 0;
+    void* d_tp = nullptr;            // two-pass chunk workspace(s)
+    size_t tp_bytes = 0;
     cufftHandle fft = 0;
     bool fft_valid = false;
     int64_t fft_n = 0, fft_batch = 0;
     int variant = -1;               // -1: not chosen (cache or default 0)
     // ragged execution (mixed N or kinds): groups of equal (N, kind), largest
     // N first, each an index list into desc; run as one CUDA graph
-    struct group { int log2n, kind; int64_t count, idx_off; };
+    struct group { int log2n, kind; int64_t count, idx_off; int64_t tp_off = -1; };
     bool ragged = false;
     std::vector<group> groups;
     std::vector<int32_t> idx;       // concatenated index lists
@@ -415,6 +417,9 @@ void release_device(lct_plan p) {
     cudaFree(p->d_desc);
     cudaFree(p->d_status);
     cudaFree(p->d_work);
+    cudaFree(p->d_tp);
+    p->d_tp = nullptr;
+    p->tp_bytes = 0;
     cudaFree(p->d_idx);
     p->d_idx = nullptr;
     cudaFree(p->d_coef);
@@ -563,6 +568,10 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
 }
 
 // Can a bulk-async variant run this plan on `in` (16-byte aligned starts)?
+// Smallest N that runs two-pass by default (measured on GB300: two passes
+// beat the cluster kernel from here up).
+constexpr int kTwoPassDefaultLog2 = 15;
+
 bool tma_aligned(lct_plan p, const void* in) {
     return ((uintptr_t)in) % 16 == 0 && (!p->is_batch || p->even_offsets);
 }
@@ -576,15 +585,76 @@ bool tma_ok(lct_plan p, const void* in) {
     return lct_fused_tma_supported(p->dtype, p->desc[0].log2n) && tma_aligned(p, in);
 }
 
+// Variant used when neither the plan nor the tune cache chooses one.
+int default_variant(lct_dtype dtype, int log2n) {
+    return (lct_twopass_supported(dtype, log2n) && log2n >= kTwoPassDefaultLog2) ? 7 : 0;
+}
+
 int effective_variant(lct_plan p) {
     if (p->variant >= 0) return p->variant;
     int v = tune_lookup(p->dtype, p->desc[0].log2n);
-    return v >= 0 ? v : 0;
+    return v >= 0 ? v : default_variant(p->dtype, p->desc[0].log2n);
+}
+
+// Two-pass path ------------------------------------------------------------
+size_t twopass_chunk_bytes() {
+    static const size_t bytes = [] {
+        const char* v = std::getenv("LCT_TWOPASS_CHUNK_MB");
+        long mb = v ? std::atol(v) : 0;
+        if (mb <= 0 || mb > 65536) mb = 1024;
+        return (size_t)mb << 20;
+    }();
+    return bytes;
+}
+
+size_t sample_bytes(lct_dtype dtype) { return dtype == LCT_C64 ? 8 : 16; }
+
+// Signals per chunk and the workspace they need for N = 2^log2n.
+int64_t twopass_chunk(lct_dtype dtype, int log2n, int64_t count) {
+    const size_t per = sample_bytes(dtype) << log2n;
+    int64_t c = (int64_t)(twopass_chunk_bytes() / per);
+    if (c < 1) c = 1;
+    return c < count ? c : count;
+}
+
+lct_status ensure_tp_work(lct_plan p, size_t need) {
+    if (need <= p->tp_bytes) return LCT_OK;
+    cudaFree(p->d_tp);
+    p->d_tp = nullptr;
+    p->tp_bytes = 0;
+    if (cudaMalloc(&p->d_tp, need) != cudaSuccess) return LCT_ERR_OOM;
+    p->tp_bytes = need;
+    return LCT_OK;
+}
+
+// Pass A then pass B over consecutive chunks of `count` signals.
+lct_status run_twopass(lct_plan p, int log2n, const void* in, void* out, int64_t count,
+                       int desc_step, const int32_t* idx, void* work, cudaStream_t stream) {
+    int l1, l2;
+    lct_twopass_split(log2n, &l1, &l2);
+    const void* tw1 = lct_twiddle_table(p->dtype, l1);
+    const void* tw2 = lct_twiddle_table(p->dtype, l2);
+    if (!tw1 || !tw2) return LCT_ERR_OOM;
+    const int64_t chunk = twopass_chunk(p->dtype, log2n, count);
+    for (int64_t first = 0; first < count; first += chunk) {
+        const int64_t n = count - first < chunk ? count - first : chunk;
+        lct_status st = from_cuda(lct_launch_twopass(p->dtype, log2n, in, out, work, p->d_desc,
+                                                     desc_step, first, n, idx, p->d_status, tw1,
+                                                     tw2, stream));
+        if (st != LCT_OK) return st;
+    }
+    return LCT_OK;
 }
 
 lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int desc_step,
                      int variant, cudaStream_t stream) {
     const int log2n = p->desc[0].log2n;
+    if (variant == 7 && lct_twopass_supported(p->dtype, log2n)) {
+        const int64_t chunk = twopass_chunk(p->dtype, log2n, batch);
+        lct_status st = ensure_tp_work(p, (size_t)chunk * (sample_bytes(p->dtype) << log2n));
+        if (st != LCT_OK) return st;
+        return run_twopass(p, log2n, in, out, batch, desc_step, nullptr, p->d_tp, stream);
+    }
     const int lm = lct_cluster_local_log2(p->dtype, log2n);
     if (lm >= 0 && (variant == 5 || !lct_fused_supported(p->dtype, log2n))) {
         const void* twl = lct_twiddle_table(p->dtype, lm);
@@ -620,6 +690,14 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
                                       nullptr, p->d_status, stream));
 }
 
+// Variant of a ragged group of N = 2^log2n: the tuned one, else the
+// default (two passes for N >= 32768).
+int group_variant(lct_dtype dtype, int log2n) {
+    const int v = tune_lookup(dtype, log2n);
+    if (v >= 0) return v;
+    return default_variant(dtype, log2n);
+}
+
 // Launch one group of a ragged plan on `stream`.
 lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, void* out,
                         cudaStream_t stream) {
@@ -630,6 +708,8 @@ lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, 
     const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
     const bool single = lct_fused_supported(p->dtype, g.log2n);
     const int v = tune_lookup(p->dtype, g.log2n);
+    if (g.tp_off >= 0)
+        return run_twopass(p, g.log2n, in, out, g.count, 1, idx, (char*)p->d_tp + g.tp_off, stream);
     if (lm >= 0 && (!single || v == 5))
         return from_cuda(lct_launch_cluster(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count,
                                             lct_twiddle_table(p->dtype, lm), idx, p->d_status,
@@ -644,7 +724,26 @@ lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, 
 // dealt round-robin (largest N first), a join; instantiated once per
 // (in, out) pair.
 lct_status build_graph(lct_plan p, const void* in, void* out) {
-    // tables first: allocation is not allowed while capturing
+    // tables and workspaces first: allocation is not allowed while capturing.
+    // Every two-pass group gets its own chunk workspace (the branches run
+    // concurrently).
+    size_t tp_need = 0;
+    for (auto& g : p->groups) {
+        g.tp_off = -1;
+        if (g.kind == LCT_KIND_DIAG || !lct_twopass_supported(p->dtype, g.log2n)) continue;
+        if (group_variant(p->dtype, g.log2n) != 7) continue;
+        int l1, l2;
+        lct_twopass_split(g.log2n, &l1, &l2);
+        if (!lct_twiddle_table(p->dtype, l1) || !lct_twiddle_table(p->dtype, l2)) return LCT_ERR_OOM;
+        g.tp_off = (int64_t)tp_need;
+        const size_t bytes = (size_t)twopass_chunk(p->dtype, g.log2n, g.count) *
+                             (sample_bytes(p->dtype) << g.log2n);
+        tp_need += (bytes + 255) & ~(size_t)255;
+    }
+    if (tp_need) {
+        lct_status st = ensure_tp_work(p, tp_need);
+        if (st != LCT_OK) return st;
+    }
     for (const auto& g : p->groups) {
         if (g.kind == LCT_KIND_DIAG) continue;
         const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
@@ -818,14 +917,15 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 6) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 7) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }
 
 lct_status lct_plan_get_variant(lct_plan plan, int* variant) {
     if (!plan || !variant) return LCT_ERR_ARG;
-    *variant = plan->variant >= 0 ? plan->variant : 0;
+    *variant = plan->variant >= 0 ? plan->variant
+                                  : default_variant(plan->dtype, plan->desc[0].log2n);
     return LCT_OK;
 }
 
@@ -843,6 +943,7 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
     if (lct_cluster_local_log2(plan->dtype, plan->desc[0].log2n) >= 0 &&
         lct_fused_supported(plan->dtype, plan->desc[0].log2n))
         candidates[n_cand++] = 5;
+    if (lct_twopass_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 7;
     if (lct_fused_pair_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 3;
     if (pair_tma_ok(plan, in)) candidates[n_cand++] = 4;
     if (tma_ok(plan, in)) {

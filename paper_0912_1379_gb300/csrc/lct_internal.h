@@ -112,6 +112,18 @@ cudaError_t lct_launch_fused_pair_tma(int dtype, int log2n, const void* in, void
                                       const void* tw_pair, int32_t* status, cudaStream_t stream);
 bool lct_fused_pair_tma_supported(int dtype, int log2n);
 
+// Two-pass large-N XFT (k_twopass.cu): N = N1 N2 with log2 N1 = log2n / 2;
+// pass A reads signals first .. first + count - 1 of the launch (through idx
+// when not null; desc_step must then be 1) and writes their column-DFT
+// results to work (count N samples); pass B writes the outputs.  tw1, tw2:
+// lct_twiddle_table(dtype, log2 N1), (dtype, log2 N2).
+bool lct_twopass_supported(int dtype, int log2n);
+void lct_twopass_split(int log2n, int* l1, int* l2);
+cudaError_t lct_launch_twopass(int dtype, int log2n, const void* in, void* out, void* work,
+                               const lct_desc* desc, int desc_step, int64_t first, int64_t count,
+                               const int32_t* idx, int32_t* status, const void* tw1,
+                               const void* tw2, cudaStream_t stream);
+
 // Split-precision XFT on the tensor cores (complex64, N = 16 .. 4096; a CTA
 // transforms 4096/N signals).  mode: 1 = split BF16 (three products),
 // 2 = split FP16 (three products, per-signal power-of-two scaling), 3 = FP16

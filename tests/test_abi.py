@@ -97,11 +97,20 @@ def test_variant_selection_host_only():
         assert lct.lct_plan_get_variant(p) == 0
         lct.lct_plan_set_variant(p, 1)
         assert lct.lct_plan_get_variant(p) == 1
+        lct.lct_plan_set_variant(p, 7)
+        assert lct.lct_plan_get_variant(p) == 7
         with pytest.raises(lct.LctError) as e:
-            lct.lct_plan_set_variant(p, 7)
+            lct.lct_plan_set_variant(p, 8)
         assert e.value.status == 1
     finally:
         lct.lct_plan_destroy(p)
+    # default: two passes from N = 32768 up, else variant 0
+    for N, want in [(4096, 0), (16384, 0), (32768, 7), (65536, 7)]:
+        p = lct.lct_plan_create(N, 1.0, 2.0, 0.5, 2.0)
+        try:
+            assert lct.lct_plan_get_variant(p) == want
+        finally:
+            lct.lct_plan_destroy(p)
 
 
 def test_precision_selection_host_only():

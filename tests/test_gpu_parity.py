@@ -105,7 +105,7 @@ def test_uniform_batch_per_signal_params(N, count, seed):
 
 
 @pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30), (16384, 9)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_kernel_variants(N, count, variant):
     """Both fused variants (one CTA per group / persistent with bulk-async
     prefetch) on per-signal parameters, with a ragged last group."""
@@ -120,6 +120,59 @@ def test_kernel_variants(N, count, variant):
     idx = np.unique(np.linspace(0, count - 1, n_check).astype(int))
     ref = O.lct(f[idx].astype(np.complex128), params[idx])
     assert rel_l2(G[idx], ref).max() < TOL32
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("log2n", [13, 14, 15, 16])
+@pytest.mark.parametrize("variant", [5, 7])
+def test_large_n_variants(dtype, log2n, variant):
+    """Large N: the cluster kernel (5, N >= 16384) and the two-pass kernels
+    (7, N >= 8192) on per-signal parameters, both precisions."""
+    if variant == 5 and log2n < 14:
+        pytest.skip("cluster kernel starts at N = 16384")
+    N, count = 1 << log2n, 3
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=log2n * 10 + variant, dtype=np.complex128)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code).set_variant(variant)
+    try:
+        G = run(p.handle, f.astype(dtype), dtype)
+    finally:
+        p.destroy()
+    idx = [0, count - 1] if log2n == 16 else list(range(count))
+    ref = O.lct(f[idx].astype(dtype).astype(np.complex128), params[idx])
+    assert rel_l2(G[idx], ref).max() < (TOL32 if dtype == np.complex64 else TOL64)
+
+
+def test_twopass_gapped_offsets():
+    """The two-pass path on signals stored with gaps (odd offsets); the gaps
+    stay untouched."""
+    N, count = 8192, 520
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=77, dtype=np.complex64)
+    stride = N + 3
+    offs = np.arange(count, dtype=np.int64) * stride
+    buf = np.zeros(count * stride, dtype=np.complex64)
+    for s in range(count):
+        buf[offs[s]:offs[s] + N] = f[s]
+    p = lct.Plan.batch([N] * count, params, offs, dtype=lct.LCT_C64).set_variant(7)
+    try:
+        xin = torch.from_numpy(buf).cuda()
+        out = torch.zeros_like(xin)
+        lct.lct_execute(p.handle, xin, out, count)
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        ob = out.cpu().numpy()
+    finally:
+        p.destroy()
+    idx = [0, 1, 510, 511, 512, 513, 519]
+    ref = O.lct(f[idx].astype(np.complex128), params[idx])
+    G = np.stack([ob[offs[s]:offs[s] + N] for s in idx])
+    assert rel_l2(G, ref).max() < TOL32
+    mask = np.ones(len(buf), dtype=bool)
+    for o in offs:
+        mask[o:o + N] = False
+    assert np.all(ob[mask] == 0)
 
 
 def test_autotune_picks_a_valid_variant():
