@@ -135,12 +135,11 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     N >= 32768 in complex64 and N >= 16384 in complex128);
  *  6  paired with eight samples per thread (radix-8 passes), fewer
  *     registers and more resident warps (complex64, N = 64 .. 8192);
- *  7  two passes over memory (four-step split N = N1 N2: column DFTs with
- *     the pre-chirp and inter-pass twiddles, then row DFTs with the
- *     post-chirp; both dtypes, N = 8192 .. 65536; the default for
- *     N >= 32768).  The intermediate goes to a plan-owned workspace of at
- *     most 1 GiB (the batch runs in chunks of that size; the environment
- *     variable LCT_TWOPASS_CHUNK_MB, read once, overrides it).
+ *  7  two passes (four-step split N = N1 N2: column DFTs with the
+ *     pre-chirp and inter-pass twiddles, then row DFTs with the post-chirp)
+ *     in one persistent launch whose intermediate stays in a small ring of
+ *     workspace slots (tens of MiB, owned by the plan), so it need not reach
+ *     HBM (both dtypes, N = 8192 .. 65536; the default for N >= 32768).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 /* The variant set on the plan, else the default for its N (7 for N >= 32768,

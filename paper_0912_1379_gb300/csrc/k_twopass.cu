@@ -1,56 +1,22 @@
-// Large-N XFT in two passes over memory (four-step factorisation of the
-// N-point DFT of Sec. 3, N = N1 N2):
+// Large-N XFT in two passes over the samples (four-step factorisation of
+// the N-point DFT of Sec. 3, N = N1 N2, log2 N1 = floor(log2 N / 2)):
 //   n = n2 + N2 n1, k = k1 + N1 k2,
 //   X[k1 + N1 k2] = sum_{n2} W_{N2}^{n2 k2} W_N^{n2 k1} sum_{n1} W_{N1}^{n1 k1} u[n2 + N2 n1]
 // with u the pre-chirped input and W_M = e^{-2 pi i / M} (forward sign).
 //
-// Pass A (a CTA per signal and group of G consecutive columns n2): loads u
-// (pre-chirp on the fly; each row n1 of the group is G consecutive samples),
-// runs the N1-point DFT down every column with the Stockham engine, multiplies
-// by W_N^{n2 k1} and stores Y[k1][n2] row-major in a workspace.
-// Pass B (a CTA per signal and group of G consecutive rows k1): N2-point DFT
-// along every row (contiguous loads), a transpose through shared memory, then
-// X[k1 + N1 k2] with the post-chirp and scale (G consecutive k1 per k2).
-//
-// Every sample is read and written twice (32 B/point for complex64); the
-// host runs the passes over chunks of signals to bound the workspace.
+// Pass A (a tile of GA consecutive columns n2 of one signal): loads u with
+// the pre-chirp (each row n1 of the tile is GA consecutive samples), runs the
+// N1-point DFT down every column with the Stockham engine, multiplies by
+// W_N^{n2 k1} and stores Y[k1][n2] row-major in a workspace slot.
+// Pass B (a tile of GB consecutive rows k1): the N2-point DFT along every
+// row (contiguous loads), a transpose through shared memory, then
+// X[k1 + N1 k2] with the post-chirp and scale (GB consecutive k1 per k2).
 #include "xft_engine.cuh"
 #include "xft_chirp.cuh"
 
 namespace {
 
 using namespace xft;
-
-constexpr int G = 16;                  // columns (pass A) or rows (pass B) per CTA
-
-template <int L1, class R>
-struct pass_a_shape {
-    static constexpr int T = shape<L1>::T;                      // threads per column
-    static constexpr int THREADS = G * T;
-    // per-column shared-memory stride: the engine's padded length plus one, an
-    // odd number of samples, so the G columns of a half-warp hit distinct banks
-    static constexpr int STR = padded_len<L1>() + 1;
-    static constexpr size_t SMEM = (size_t)G * STR * sizeof(cpx<R>);
-};
-
-template <int L2, class R>
-struct pass_b_shape {
-    static constexpr int T = shape<L2>::T;                      // threads per row
-    static constexpr int THREADS = G * T;
-    static constexpr int NP = padded_len<L2>();
-    // the transpose tile [N2][G + 1] reuses the engine buffers
-    static constexpr size_t ENGINE = (size_t)G * NP;
-    static constexpr size_t TILE = (size_t)(1 << L2) * (G + 1);
-    static constexpr size_t SMEM = (ENGINE > TILE ? ENGINE : TILE) * sizeof(cpx<R>);
-};
-
-// Resident threads per SM for the register budget: 1024 (complex64, <= 64
-// registers), 512 (complex128, <= 128).
-template <class R, int THREADS>
-constexpr int tp_min_blocks() {
-    constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
-    return per_sm / THREADS > 0 ? per_sm / THREADS : 1;
-}
 
 template <int LN, class R>
 __device__ __forceinline__ cpx<R> pre_tp(const lct_desc& D, int n, bool decay) {
@@ -63,7 +29,7 @@ __device__ __forceinline__ cpx<R> post_tp(const lct_desc& D, int n) {
     else return post_chirp64<LN>(D, n);
 }
 
-// Descriptor of signal `first + j` of the launch (through idx for ragged
+// Descriptor of signal `sig` of the launch (through idx for ragged
 // batches); a descriptor that does not match the kernel is flagged, and the
 // signal skipped.
 template <int LN>
@@ -80,124 +46,251 @@ __device__ __forceinline__ bool tp_signal(const lct_desc* __restrict__ desc, int
     return true;
 }
 
-template <int L1, int L2, class R>
-__global__ void __launch_bounds__(pass_a_shape<L1, R>::THREADS,
-                                  (tp_min_blocks<R, pass_a_shape<L1, R>::THREADS>()))
-k_xft_pass_a(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ work,
-             const lct_desc* __restrict__ desc, int desc_step, int64_t first,
-             const int32_t* __restrict__ idx, int32_t* __restrict__ status,
-             const cpx<R>* __restrict__ tw1) {
-    using S1 = shape<L1>;
-    using A = pass_a_shape<L1, R>;
-    constexpr int LN = L1 + L2, N = 1 << LN, N2 = 1 << L2, CB = N2 / G, T1 = S1::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int tid = threadIdx.x, s = tid % G, i = tid / G;
-    const int64_t j = blockIdx.x / CB;                  // signal within the chunk
-    const int n2 = (int)(blockIdx.x % CB) * G + s;      // this thread's column
-    lct_desc D;
-    int64_t base;
-    const bool active = tp_signal<LN>(desc, desc_step, first + j, idx, status, D, base);
-    const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+// ---------------------------------------------------------------------------
+// Persistent single-launch form: one grid of PT_THREADS-thread CTAs takes
+// work items from a queue, pass-A tiles (GA columns) and pass-B tiles (GB
+// rows) in the order
+//   step t: the A tiles of signal t, then the B tiles of signal t - D,
+// and keeps the intermediate of W = D + 2 signals in a ring of workspace
+// slots (signal t in slot t mod W), small enough to stay in L2.  Per-slot
+// counters (monotone over the launch) order the two passes: a B tile of
+// signal s waits until all CB A tiles of s are stored; an A tile of signal
+// t >= W waits until the RB B tiles of signal t - W have read the slot.
+// Every wait is on items taken from the queue earlier, so it always ends;
+// waits are bounded anyway (a timeout is recorded, never a hang).
+// ---------------------------------------------------------------------------
+constexpr int PT_THREADS = 256;
+constexpr uint64_t kPtWaitNs = 2000000000ull;   // 2 s
 
-    cpx<R> v[S1::E];
-#pragma unroll
-    for (int e = 0; e < S1::E; ++e) {
-        const int n = n2 + N2 * (i + e * T1);
-        cpx<R> f = {R(0), R(0)};
-        if (active) f = ld_stream(in + base + n);
-        v[e] = cmul(f, pre_tp<LN, R>(D, n, decay));
-    }
-    dft_signal<L1, -1>(v, smem + s * A::STR, i, tw1);
-    // inter-pass twiddle W_N^{n2 k1}, k1 = i + e T1: W_N^{n2 i} times the
-    // powers of W_N^{n2 T1} (product tree, a few roundings deep)
-    const cpx<R> w0 = twiddle_exact<R, -1>((n2 * i) & (N - 1), N);
-    cpx<R> ws[S1::E];
-    twiddle_powers<S1::E>(twiddle_exact<R, -1>((n2 * T1) & (N - 1), N), ws);
-    if (active) {
-        cpx<R>* y = work + j * (int64_t)N + n2;
-#pragma unroll
-        for (int e = 0; e < S1::E; ++e) y[(i + e * T1) * N2] = cmul(v[e], cmul(w0, ws[e]));
-    }
+template <int L1, int L2, class R>
+struct pt_shape {
+    static constexpr int LN = L1 + L2, N = 1 << LN, N1 = 1 << L1, N2 = 1 << L2;
+    static constexpr int T1 = shape<L1>::T, T2 = shape<L2>::T;
+    static constexpr int GA = PT_THREADS / T1;            // columns per A tile
+    static constexpr int GB = PT_THREADS / T2;            // rows per B tile
+    static constexpr int CB = N2 / GA, RB = N1 / GB;      // A and B tiles per signal
+    static constexpr int STR = padded_len<L1>() + 1;      // odd: column buffers on distinct banks
+    static constexpr int NPB = padded_len<L2>();
+    static constexpr int TS = GB + 16 / T2;               // transpose row stride (conflict-free)
+    static constexpr size_t SA = (size_t)GA * STR, SB1 = (size_t)GB * NPB, SB2 = (size_t)N2 * TS;
+    static constexpr size_t ELEMS = SA > SB1 ? (SA > SB2 ? SA : SB2) : (SB1 > SB2 ? SB1 : SB2);
+    static constexpr size_t SMEM = ELEMS * sizeof(cpx<R>);
+    static_assert(CB >= 1 && RB >= 1, "tile larger than the signal");
+};
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-template <int L1, int L2, class R>
-__global__ void __launch_bounds__(pass_b_shape<L2, R>::THREADS,
-                                  (tp_min_blocks<R, pass_b_shape<L2, R>::THREADS>()))
-k_xft_pass_b(const cpx<R>* __restrict__ work, cpx<R>* __restrict__ out,
-             const lct_desc* __restrict__ desc, int desc_step, int64_t first,
-             const int32_t* __restrict__ idx, int32_t* __restrict__ status,
-             const cpx<R>* __restrict__ tw2) {
-    using S2 = shape<L2>;
-    using B = pass_b_shape<L2, R>;
-    constexpr int LN = L1 + L2, N = 1 << LN, N1 = 1 << L1, N2 = S2::N, RB = N1 / G, T2 = S2::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
-    const int tid = threadIdx.x, r = tid / T2, i = tid % T2;
-    const int64_t j = blockIdx.x / RB;
-    const int k1b = (int)(blockIdx.x % RB) * G;          // first row of the group
-    lct_desc D;
-    int64_t base;
-    const bool active = tp_signal<LN>(desc, desc_step, first + j, idx, status, D, base);
-
-    cpx<R> v[S2::E];
-    const cpx<R>* y = work + j * (int64_t)N + (int64_t)(k1b + r) * N2;
-#pragma unroll
-    for (int e = 0; e < S2::E; ++e) v[e] = ld_stream(y + i + e * T2);
-    dft_signal<L2, -1>(v, smem + r * B::NP, i, tw2);
-    __syncthreads();                                     // engine buffers free
-#pragma unroll
-    for (int e = 0; e < S2::E; ++e) smem[(i + e * T2) * (G + 1) + r] = v[e];
-    __syncthreads();
-    if (!active) return;
-    const R sc = (R)D.scale;
-    const int rr = tid % G, q = tid / G;                 // row k1b + rr, k2 = q + e T2
-#pragma unroll
-    for (int e = 0; e < S2::E; ++e) {
-        const int k2 = q + e * T2;
-        const int k = k1b + rr + N1 * k2;
-        out[base + k] = cscale(cmul(smem[k2 * (G + 1) + rr], post_tp<LN, R>(D, k)), sc);
+// Bounded wait for *ctr >= target (thread 0 of the CTA); false on timeout.
+// A timeout anywhere in the launch raises the launch's abort flag, and every
+// later wait then gives up at once, so a fault in the ordering costs one
+// bound, not one per item.
+__device__ __forceinline__ bool wait_geq(const int32_t* ctr, int32_t target, int32_t* abort_flag) {
+    if (ld_acquire(ctr) >= target) return true;
+    if (ld_acquire(abort_flag)) return false;
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        __nanosleep(100);
+        if (ld_acquire(ctr) >= target) return true;
+        if ((it & 255) == 255 && ld_acquire(abort_flag)) return false;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > kPtWaitNs) break;
     }
-}
-
-template <int L1, int L2, class R>
-cudaError_t launch_tp(const void* in, void* out, void* work, const lct_desc* desc, int desc_step,
-                      int64_t first, int64_t count, const int32_t* idx, int32_t* status,
-                      const void* tw1, const void* tw2, cudaStream_t stream) {
-    using A = pass_a_shape<L1, R>;
-    using B = pass_b_shape<L2, R>;
-    constexpr int N1 = 1 << L1, N2 = 1 << L2;
-    auto ka = k_xft_pass_a<L1, L2, R>;
-    auto kb = k_xft_pass_b<L1, L2, R>;
-    cudaError_t e;
-    if (A::SMEM > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::SMEM)) != cudaSuccess)
-        return e;
-    if (B::SMEM > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM)) != cudaSuccess)
-        return e;
-    const int64_t blocks_a = count * (N2 / G), blocks_b = count * (N1 / G);
-    if (blocks_a > 0x7fffffffLL || blocks_b > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    ka<<<(unsigned)blocks_a, A::THREADS, A::SMEM, stream>>>(
-        (const cpx<R>*)in, (cpx<R>*)work, desc, desc_step, first, idx, status, (const cpx<R>*)tw1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    kb<<<(unsigned)blocks_b, B::THREADS, B::SMEM, stream>>>(
-        (const cpx<R>*)work, (cpx<R>*)out, desc, desc_step, first, idx, status, (const cpx<R>*)tw2);
-    return cudaGetLastError();
+    atomicExch(abort_flag, 1);
+    return false;
 }
 
 template <class R>
-cudaError_t tp_dispatch(int log2n, const void* in, void* out, void* work, const lct_desc* desc,
-                        int desc_step, int64_t first, int64_t count, const int32_t* idx,
-                        int32_t* status, const void* tw1, const void* tw2, cudaStream_t stream) {
-    switch (log2n) {
-        case 13: return launch_tp<6, 7, R>(in, out, work, desc, desc_step, first, count, idx, status, tw1, tw2, stream);
-        case 14: return launch_tp<7, 7, R>(in, out, work, desc, desc_step, first, count, idx, status, tw1, tw2, stream);
-        case 15: return launch_tp<7, 8, R>(in, out, work, desc, desc_step, first, count, idx, status, tw1, tw2, stream);
-        case 16: return launch_tp<8, 8, R>(in, out, work, desc, desc_step, first, count, idx, status, tw1, tw2, stream);
-        default: return cudaErrorInvalidValue;
+__device__ __forceinline__ cpx<R> ld_l2(const cpx<R>* p);
+template <>
+__device__ __forceinline__ cpx<float> ld_l2<float>(const cpx<float>* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+template <>
+__device__ __forceinline__ cpx<double> ld_l2<double>(const cpx<double>* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
+
+template <int L1, int L2, class R>
+__global__ void __launch_bounds__(PT_THREADS, (sizeof(R) == 4 ? 4 : 2))
+k_xft_twopass(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, cpx<R>* __restrict__ work,
+              int32_t* __restrict__ sync, const lct_desc* __restrict__ desc, int desc_step,
+              int64_t count, int64_t lag, int64_t slots, const int32_t* __restrict__ idx,
+              int32_t* __restrict__ status, const cpx<R>* __restrict__ tw1,
+              const cpx<R>* __restrict__ tw2) {
+    using P = pt_shape<L1, L2, R>;
+    constexpr int LN = P::LN, N = P::N, N1 = P::N1, N2 = P::N2, T1 = P::T1, T2 = P::T2;
+    constexpr int GA = P::GA, GB = P::GB, CB = P::CB, RB = P::RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
+    __shared__ long long s_item;
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(sync);
+    int32_t* abort_flag = sync + 2;
+    int32_t* cnt_a = sync + 4;
+    int32_t* cnt_b = cnt_a + slots;
+    const int tid = threadIdx.x;
+    const int64_t total = count * (CB + RB);
+    const int64_t a_head = lag * CB, mid = (count - lag) * (CB + RB);
+
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        int64_t p = s_item;
+        if (p >= total) break;
+        // decode: pass, signal, tile
+        bool is_a;
+        int64_t sig;
+        int tile;
+        if (p < a_head) {
+            is_a = true; sig = p / CB; tile = (int)(p % CB);
+        } else if ((p -= a_head) < mid) {
+            const int64_t t = lag + p / (CB + RB);
+            const int r = (int)(p % (CB + RB));
+            is_a = r < CB;
+            sig = is_a ? t : t - lag;
+            tile = is_a ? r : r - CB;
+        } else {
+            p -= mid;
+            is_a = false; sig = count - lag + p / RB; tile = (int)(p % RB);
+        }
+        const int64_t slot = sig % slots;
+        const int32_t round = (int32_t)(sig / slots);       // earlier occupants of the slot
+        cpx<R>* y = work + slot * (int64_t)N;
+        lct_desc D;
+        int64_t base;
+        const bool active = tp_signal<LN>(desc, desc_step, sig, idx, status, D, base);
+
+        if (is_a) {
+            const int s = tid % GA, i = tid / GA;
+            const int n2 = tile * GA + s;
+            const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+            cpx<R> v[shape<L1>::E];
+#pragma unroll
+            for (int e = 0; e < shape<L1>::E; ++e) {
+                const int n = n2 + N2 * (i + e * T1);
+                cpx<R> f = {R(0), R(0)};
+                if (active) f = ld_stream(in + base + n);
+                v[e] = cmul(f, pre_tp<LN, R>(D, n, decay));
+            }
+            dft_signal<L1, -1>(v, smem + s * P::STR, i, tw1);
+            const cpx<R> w0 = twiddle_exact<R, -1>((n2 * i) & (N - 1), N);
+            cpx<R> ws[shape<L1>::E];
+            twiddle_powers<shape<L1>::E>(twiddle_exact<R, -1>((n2 * T1) & (N - 1), N), ws);
+            // the slot is free once the previous occupant's B tiles have read it
+            if (tid == 0 && round > 0 && !wait_geq(cnt_b + slot, round * RB, abort_flag))
+                atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < shape<L1>::E; ++e)
+                y[(i + e * T1) * N2 + n2] = cmul(v[e], cmul(w0, ws[e]));
+            __syncthreads();                             // stores issued, shared memory free
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(cnt_a + slot, 1);
+            }
+        } else {
+            const int r = tid / T2, i = tid % T2;
+            if (tid == 0 && !wait_geq(cnt_a + slot, (round + 1) * CB, abort_flag))
+                atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
+            __syncthreads();
+            const int k1b = tile * GB;
+            cpx<R> v[shape<L2>::E];
+            const cpx<R>* row = y + (int64_t)(k1b + r) * N2;
+#pragma unroll
+            for (int e = 0; e < shape<L2>::E; ++e) v[e] = ld_l2<R>(row + i + e * T2);
+            dft_signal<L2, -1>(v, smem + r * P::NPB, i, tw2);
+            __syncthreads();                             // slot read, engine buffers free
+            if (tid == 0) atomicAdd(cnt_b + slot, 1);
+#pragma unroll
+            for (int e = 0; e < shape<L2>::E; ++e) smem[(i + e * T2) * P::TS + r] = v[e];
+            __syncthreads();
+            if (active) {
+                const R sc = (R)D.scale;
+                const int rr = tid % GB, q = tid / GB;   // row k1b + rr, k2 = q + e T2
+#pragma unroll
+                for (int e = 0; e < shape<L2>::E; ++e) {
+                    const int k2 = q + e * T2;
+                    const int k = k1b + rr + N1 * k2;
+                    out[base + k] = cscale(cmul(smem[k2 * P::TS + rr], post_tp<LN, R>(D, k)), sc);
+                }
+            }
+            __syncthreads();                             // shared memory free for the next item
+        }
     }
 }
+
+// Grid of the persistent kernel on the current device (resident CTAs).
+template <int L1, int L2, class R>
+cudaError_t pt_grid(int64_t* grid) {
+    using P = pt_shape<L1, L2, R>;
+    auto kern = k_xft_twopass<L1, L2, R>;
+    static int per_sm[64] = {}, sms[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!per_sm[dev]) {
+        if (P::SMEM > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM)) != cudaSuccess)
+            return e;
+        int nb = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, PT_THREADS, P::SMEM)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        per_sm[dev] = nb > 0 ? nb : 1;
+    }
+    *grid = (int64_t)per_sm[dev] * sms[dev];
+    return cudaSuccess;
+}
+
+// Lag D (signals) and ring slots W = D + 2 for `count` signals: the B tiles
+// trail by about twice the number of tiles in flight.
+template <int L1, int L2, class R>
+cudaError_t pt_ring(int64_t count, int64_t* lag, int64_t* slots) {
+    using P = pt_shape<L1, L2, R>;
+    int64_t grid = 0;
+    cudaError_t e = pt_grid<L1, L2, R>(&grid);
+    if (e != cudaSuccess) return e;
+    int64_t d = (2 * grid + (P::CB + P::RB) - 1) / (P::CB + P::RB);
+    if (d < 2) d = 2;
+    if (d > count) d = count;
+    *lag = d;
+    *slots = d + 2;
+    return cudaSuccess;
+}
+
+template <int L1, int L2, class R>
+cudaError_t launch_pt(const void* in, void* out, void* work, int32_t* sync, const lct_desc* desc,
+                      int desc_step, int64_t count, const int32_t* idx, int32_t* status,
+                      const void* tw1, const void* tw2, cudaStream_t stream) {
+    using P = pt_shape<L1, L2, R>;
+    int64_t grid = 0, lag = 0, slots = 0;
+    cudaError_t e = pt_grid<L1, L2, R>(&grid);
+    if (e != cudaSuccess) return e;
+    if ((e = pt_ring<L1, L2, R>(count, &lag, &slots)) != cudaSuccess) return e;
+    const int64_t total = count * (P::CB + P::RB);
+    if (grid > total) grid = total;
+    if ((e = cudaMemsetAsync(sync, 0, (size_t)(4 + 2 * slots) * sizeof(int32_t), stream)) != cudaSuccess)
+        return e;
+    k_xft_twopass<L1, L2, R><<<(unsigned)grid, PT_THREADS, P::SMEM, stream>>>(
+        (const cpx<R>*)in, (cpx<R>*)out, (cpx<R>*)work, sync, desc, desc_step, count, lag, slots,
+        idx, status, (const cpx<R>*)tw1, (const cpx<R>*)tw2);
+    return cudaGetLastError();
+}
+
+#define LCT_TP_SIZES(X, R) \
+    case 13: X(6, 7, R)    \
+    case 14: X(7, 7, R)    \
+    case 15: X(7, 8, R)    \
+    case 16: X(8, 8, R)
 
 }  // namespace
 
@@ -211,14 +304,30 @@ void lct_twopass_split(int log2n, int* l1, int* l2) {
     *l2 = log2n - log2n / 2;
 }
 
+// Ring workspace of the persistent form: `slots` signals of N samples, plus
+// (4 + 2 slots) int32 of queue, abort flag and counters.
+cudaError_t lct_twopass_ring(int dtype, int log2n, int64_t count, int64_t* slots) {
+    int64_t lag = 0;
+    *slots = 0;
+    if (count <= 0) return cudaSuccess;
+#define LCT_TP_RING(A, B, R) return pt_ring<A, B, R>(count, &lag, slots);
+    if (dtype == 0) {
+        switch (log2n) { LCT_TP_SIZES(LCT_TP_RING, float) default: return cudaErrorInvalidValue; }
+    }
+    switch (log2n) { LCT_TP_SIZES(LCT_TP_RING, double) default: return cudaErrorInvalidValue; }
+#undef LCT_TP_RING
+}
+
 cudaError_t lct_launch_twopass(int dtype, int log2n, const void* in, void* out, void* work,
-                               const lct_desc* desc, int desc_step, int64_t first, int64_t count,
+                               int32_t* sync, const lct_desc* desc, int desc_step, int64_t count,
                                const int32_t* idx, int32_t* status, const void* tw1,
                                const void* tw2, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
-    if (dtype == 0)
-        return tp_dispatch<float>(log2n, in, out, work, desc, desc_step, first, count, idx, status,
-                                  tw1, tw2, stream);
-    return tp_dispatch<double>(log2n, in, out, work, desc, desc_step, first, count, idx, status,
-                               tw1, tw2, stream);
+#define LCT_TP_LAUNCH(A, B, R) \
+    return launch_pt<A, B, R>(in, out, work, sync, desc, desc_step, count, idx, status, tw1, tw2, stream);
+    if (dtype == 0) {
+        switch (log2n) { LCT_TP_SIZES(LCT_TP_LAUNCH, float) default: return cudaErrorInvalidValue; }
+    }
+    switch (log2n) { LCT_TP_SIZES(LCT_TP_LAUNCH, double) default: return cudaErrorInvalidValue; }
+#undef LCT_TP_LAUNCH
 }

@@ -597,24 +597,16 @@ int effective_variant(lct_plan p) {
 }
 
 // Two-pass path ------------------------------------------------------------
-size_t twopass_chunk_bytes() {
-    static const size_t bytes = [] {
-        const char* v = std::getenv("LCT_TWOPASS_CHUNK_MB");
-        long mb = v ? std::atol(v) : 0;
-        if (mb <= 0 || mb > 65536) mb = 1024;
-        return (size_t)mb << 20;
-    }();
-    return bytes;
-}
-
 size_t sample_bytes(lct_dtype dtype) { return dtype == LCT_C64 ? 8 : 16; }
 
-// Signals per chunk and the workspace they need for N = 2^log2n.
-int64_t twopass_chunk(lct_dtype dtype, int log2n, int64_t count) {
-    const size_t per = sample_bytes(dtype) << log2n;
-    int64_t c = (int64_t)(twopass_chunk_bytes() / per);
-    if (c < 1) c = 1;
-    return c < count ? c : count;
+// Workspace bytes of the two-pass path for `count` signals of N = 2^log2n:
+// the ring slots, then the queue and counters.
+lct_status twopass_work_bytes(lct_dtype dtype, int log2n, int64_t count, size_t* bytes) {
+    int64_t slots = 0;
+    if (lct_twopass_ring(dtype, log2n, count, &slots) != cudaSuccess) return LCT_ERR_CUDA;
+    *bytes = (size_t)slots * (sample_bytes(dtype) << log2n) +
+             (((size_t)(4 + 2 * slots) * 4 + 255) & ~(size_t)255);
+    return LCT_OK;
 }
 
 lct_status ensure_tp_work(lct_plan p, size_t need) {
@@ -627,7 +619,8 @@ lct_status ensure_tp_work(lct_plan p, size_t need) {
     return LCT_OK;
 }
 
-// Pass A then pass B over consecutive chunks of `count` signals.
+// The two-pass transform of `count` signals with the workspace `work` (of
+// twopass_work_bytes bytes).
 lct_status run_twopass(lct_plan p, int log2n, const void* in, void* out, int64_t count,
                        int desc_step, const int32_t* idx, void* work, cudaStream_t stream) {
     int l1, l2;
@@ -635,23 +628,20 @@ lct_status run_twopass(lct_plan p, int log2n, const void* in, void* out, int64_t
     const void* tw1 = lct_twiddle_table(p->dtype, l1);
     const void* tw2 = lct_twiddle_table(p->dtype, l2);
     if (!tw1 || !tw2) return LCT_ERR_OOM;
-    const int64_t chunk = twopass_chunk(p->dtype, log2n, count);
-    for (int64_t first = 0; first < count; first += chunk) {
-        const int64_t n = count - first < chunk ? count - first : chunk;
-        lct_status st = from_cuda(lct_launch_twopass(p->dtype, log2n, in, out, work, p->d_desc,
-                                                     desc_step, first, n, idx, p->d_status, tw1,
-                                                     tw2, stream));
-        if (st != LCT_OK) return st;
-    }
-    return LCT_OK;
+    int64_t slots = 0;
+    if (lct_twopass_ring(p->dtype, log2n, count, &slots) != cudaSuccess) return LCT_ERR_CUDA;
+    int32_t* sync = (int32_t*)((char*)work + (size_t)slots * (sample_bytes(p->dtype) << log2n));
+    return from_cuda(lct_launch_twopass(p->dtype, log2n, in, out, work, sync, p->d_desc,
+                                        desc_step, count, idx, p->d_status, tw1, tw2, stream));
 }
 
 lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int desc_step,
                      int variant, cudaStream_t stream) {
     const int log2n = p->desc[0].log2n;
     if (variant == 7 && lct_twopass_supported(p->dtype, log2n)) {
-        const int64_t chunk = twopass_chunk(p->dtype, log2n, batch);
-        lct_status st = ensure_tp_work(p, (size_t)chunk * (sample_bytes(p->dtype) << log2n));
+        size_t need = 0;
+        lct_status st = twopass_work_bytes(p->dtype, log2n, batch, &need);
+        if (st == LCT_OK) st = ensure_tp_work(p, need);
         if (st != LCT_OK) return st;
         return run_twopass(p, log2n, in, out, batch, desc_step, nullptr, p->d_tp, stream);
     }
@@ -736,8 +726,9 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
         lct_twopass_split(g.log2n, &l1, &l2);
         if (!lct_twiddle_table(p->dtype, l1) || !lct_twiddle_table(p->dtype, l2)) return LCT_ERR_OOM;
         g.tp_off = (int64_t)tp_need;
-        const size_t bytes = (size_t)twopass_chunk(p->dtype, g.log2n, g.count) *
-                             (sample_bytes(p->dtype) << g.log2n);
+        size_t bytes = 0;
+        lct_status st = twopass_work_bytes(p->dtype, g.log2n, g.count, &bytes);
+        if (st != LCT_OK) return st;
         tp_need += (bytes + 255) & ~(size_t)255;
     }
     if (tp_need) {

@@ -112,15 +112,18 @@ cudaError_t lct_launch_fused_pair_tma(int dtype, int log2n, const void* in, void
                                       const void* tw_pair, int32_t* status, cudaStream_t stream);
 bool lct_fused_pair_tma_supported(int dtype, int log2n);
 
-// Two-pass large-N XFT (k_twopass.cu): N = N1 N2 with log2 N1 = log2n / 2;
-// pass A reads signals first .. first + count - 1 of the launch (through idx
-// when not null; desc_step must then be 1) and writes their column-DFT
-// results to work (count N samples); pass B writes the outputs.  tw1, tw2:
-// lct_twiddle_table(dtype, log2 N1), (dtype, log2 N2).
+// Two-pass large-N XFT (k_twopass.cu), one persistent launch: N = N1 N2
+// with log2 N1 = log2n / 2 (lct_twopass_split); tw1, tw2:
+// lct_twiddle_table(dtype, log2 N1), (dtype, log2 N2).  work: `slots` ring
+// slots of N samples (lct_twopass_ring); sync: the queue, abort flag and
+// counters (4 + 2 slots int32, 8-byte aligned), zeroed by the launch.
+// Signal s of the launch is descriptor idx[s] when idx is not null
+// (desc_step must then be 1).  A timed-out wait records LCT_DEV_TIMEOUT.
 bool lct_twopass_supported(int dtype, int log2n);
 void lct_twopass_split(int log2n, int* l1, int* l2);
+cudaError_t lct_twopass_ring(int dtype, int log2n, int64_t count, int64_t* slots);
 cudaError_t lct_launch_twopass(int dtype, int log2n, const void* in, void* out, void* work,
-                               const lct_desc* desc, int desc_step, int64_t first, int64_t count,
+                               int32_t* sync, const lct_desc* desc, int desc_step, int64_t count,
                                const int32_t* idx, int32_t* status, const void* tw1,
                                const void* tw2, cudaStream_t stream);
 
