@@ -165,6 +165,19 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
 lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                        lct_stream_t stream);
 
+/* lct_execute on host buffers: h_in/h_out are host memory (page-locked for
+ * overlap; pageable memory works but each copy then blocks the host).  The
+ * batch is split into chunks of about 32 MiB that are copied in, transformed
+ * and copied out on three plan-owned streams with two plan-owned device
+ * staging pairs, so the copies in both directions overlap each other and the
+ * kernels.  Ordered after the work already queued on `stream`; `stream`
+ * waits for the last copy-out (the call itself returns after queueing).
+ * Calls on one plan must be ordered (one stream).  Plans from
+ * lct_plan_create[_complex] or batch plans of one N with offset[s] = s N;
+ * LCT_ERR_UNSUPPORTED otherwise. */
+lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
+                            lct_stream_t stream);
+
 /* Discrete fractional Fourier transform F_z with the normalisation of
  * eq. (eqifft): F_z = sqrt(2/(1 - z^2)) sqrt(2 pi i b) LCT(a, b, c, d) with
  * a = d = (z + 1/z)/2, b = (1/z - z)/(2i), c = i (1/z - z)/2, for

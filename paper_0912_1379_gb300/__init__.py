@@ -63,6 +63,7 @@ def _load():
             "lct_plan_create_batch": [plan_p, i64, lp, dp, lp, i32],
             "lct_plan_set_precision": [vp, i32],
             "lct_execute": [vp, vp, vp, i64, vp],
+            "lct_execute_host": [vp, vp, vp, i64, vp],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
@@ -188,6 +189,13 @@ def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
            "lct_execute")
 
 
+def lct_execute_host(plan: int, h_in, h_out, batch: int, stream=None) -> None:
+    """lct_execute on host buffers (page-locked tensors for overlap): the
+    library pipelines copy-in, transform and copy-out over chunks."""
+    _check(_load().lct_execute_host(plan, _ptr(h_in), _ptr(h_out), batch, _stream_handle(stream)),
+           "lct_execute_host")
+
+
 def lct_backward(plan: int, grad_out, inp, out, grad_in, grad_abd, batch: int, stream=None) -> None:
     """grad_in = L^H grad_out; grad_abd (float64 device tensor or None)
     receives (dl/da, dl/db, dl/dd) per signal (batch plans) or summed."""
@@ -307,6 +315,9 @@ class Plan:
 
     def execute(self, inp, out, batch: int, stream=None) -> None:
         lct_execute(self.handle, inp, out, batch, stream)
+
+    def execute_host(self, h_in, h_out, batch: int, stream=None) -> None:
+        lct_execute_host(self.handle, h_in, h_out, batch, stream)
 
     def set_variant(self, variant: int) -> "Plan":
         lct_plan_set_variant(self.handle, variant)

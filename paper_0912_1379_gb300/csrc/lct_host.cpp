@@ -316,6 +316,13 @@ struct lct_plan_s {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kBranches] = {};
     cudaGraphExec_t gexec = nullptr;
+    // host-buffer execution: copy-in, compute and copy-out streams, two
+    // staging buffer pairs of `hx_chunk` signals, and their events
+    cudaStream_t hx_stream[3] = {};
+    cudaEvent_t hx_start = nullptr;
+    cudaEvent_t hx_in[2] = {}, hx_comp[2] = {}, hx_out[2] = {};
+    void* hx_buf = nullptr;
+    size_t hx_bytes = 0;
     const void* g_in = nullptr;
     void* g_out = nullptr;
     // backward: per-signal gradient coefficients and reduction workspace
@@ -407,6 +414,21 @@ void release_device(lct_plan p) {
         p->side[b] = nullptr;
         p->ev_join[b] = nullptr;
     }
+    for (int k = 0; k < 3; ++k) {
+        if (p->hx_stream[k]) cudaStreamDestroy(p->hx_stream[k]);
+        p->hx_stream[k] = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        for (cudaEvent_t* e : {&p->hx_in[b], &p->hx_comp[b], &p->hx_out[b]}) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+    }
+    if (p->hx_start) cudaEventDestroy(p->hx_start);
+    p->hx_start = nullptr;
+    cudaFree(p->hx_buf);
+    p->hx_buf = nullptr;
+    p->hx_bytes = 0;
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     p->cap = nullptr;
@@ -857,6 +879,75 @@ lct_status run_ragged(lct_plan p, const void* in, void* out, cudaStream_t stream
     return from_cuda(cudaGraphLaunch(p->gexec, stream));
 }
 
+// The transform on the current device with the plan's state set up (lock
+// held).  desc: the descriptors of the launch's signals (the plan's, or a
+// sub-range of them for chunked execution; batch plans address samples by
+// each descriptor's offset into in/out).
+lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, void* out,
+                          int64_t batch, cudaStream_t stream) {
+    if (plan->ragged) return run_ragged(plan, in, out, stream);
+    // every path below reads the descriptors through plan->d_desc
+    struct swap {
+        lct_plan p;
+        lct_desc* saved;
+        ~swap() { p->d_desc = saved; }
+    } restore{plan, plan->d_desc};
+    plan->d_desc = const_cast<lct_desc*>(desc);
+    const int desc_step = plan->is_batch ? 1 : 0;
+    const lct_desc& D0 = plan->desc[0];
+    const int log2n = D0.log2n;
+    if (D0.kind == LCT_KIND_DIAG)
+        return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
+                                         batch, nullptr, plan->d_status, stream));
+    if (plan->prec == LCT_PREC_PLAIN64) {
+        // the plain path assumes contiguous rows
+        if (plan->is_batch && !plan->contiguous) return LCT_ERR_UNSUPPORTED;
+        return run_plain(plan, in, out, batch, desc_step, stream);
+    }
+    if (plan->prec == LCT_PREC_SPLIT_BF16 || plan->prec == LCT_PREC_SPLIT_FP16 ||
+        plan->prec == LCT_PREC_FP16) {
+        const void* tw = lct_twiddle_table(plan->dtype, log2n);
+        if (log2n >= 5 && !tw) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_split((int)plan->prec, log2n, in, out, plan->d_desc,
+                                          desc_step, batch, tw, tma_aligned(plan, in) ? 1 : 0,
+                                          plan->contiguous ? 1 : 0, plan->d_status, stream));
+    }
+    return run_fused(plan, in, out, batch, desc_step, effective_variant(plan), stream);
+}
+
+// Host-buffer execution ----------------------------------------------------
+// Signals per chunk: about 32 MiB of samples, at least one signal (measured
+// on GB300 with 512 MiB each way: 16 MiB 3.62 ms, 32 MiB 3.46 ms, 64 MiB
+// 3.52 ms, 128 MiB 5.66 ms -- fill and drain against too few chunks).
+int64_t host_chunk(const lct_plan p) {
+    const size_t per = (size_t)p->N0 * sample_bytes(p->dtype);
+    int64_t c = (int64_t)(((size_t)32 << 20) / per);
+    return c < 1 ? 1 : c;
+}
+
+lct_status ensure_host_state(lct_plan p, int64_t chunk) {
+    if (!p->hx_stream[0]) {
+        for (int k = 0; k < 3; ++k)
+            if (cudaStreamCreateWithFlags(&p->hx_stream[k], cudaStreamNonBlocking) != cudaSuccess)
+                return LCT_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&p->hx_start, cudaEventDisableTiming) != cudaSuccess)
+            return LCT_ERR_CUDA;
+        for (int b = 0; b < 2; ++b)
+            for (cudaEvent_t* e : {&p->hx_in[b], &p->hx_comp[b], &p->hx_out[b]})
+                if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+                    return LCT_ERR_CUDA;
+    }
+    const size_t need = 4 * (size_t)chunk * (size_t)p->N0 * sample_bytes(p->dtype);
+    if (need > p->hx_bytes) {
+        cudaFree(p->hx_buf);
+        p->hx_buf = nullptr;
+        p->hx_bytes = 0;
+        if (cudaMalloc(&p->hx_buf, need) != cudaSuccess) return LCT_ERR_OOM;
+        p->hx_bytes = need;
+    }
+    return LCT_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -990,34 +1081,71 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
     if (st != LCT_OK) return st;
     st = check_ptr(out, plan->dtype);
     if (st != LCT_OK) return st;
-    cudaStream_t stream = (cudaStream_t)stream_;
     std::lock_guard<std::mutex> g(plan->mu);
     st = ensure_device(plan);
     if (st != LCT_OK) return st;
-    int desc_step = plan->is_batch ? 1 : 0;
-    if (plan->ragged) return run_ragged(plan, in, out, stream);
-    const lct_desc& D0 = plan->desc[0];
-    int log2n = D0.log2n;
-    if (D0.kind == LCT_KIND_DIAG)
-        return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
-                                         batch, nullptr, plan->d_status, stream));
-    if (plan->prec == LCT_PREC_PLAIN64) {
+    return execute_locked(plan, plan->d_desc, in, out, batch, (cudaStream_t)stream_);
+}
+
+lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
+                            lct_stream_t stream_) {
+    if (!plan || !h_in || !h_out || batch < 0) return LCT_ERR_ARG;
+    if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
+    if (batch == 0) return LCT_OK;
+    if (plan->ragged || plan->N0 == 0 || (plan->is_batch && !plan->contiguous))
+        return LCT_ERR_UNSUPPORTED;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    std::lock_guard<std::mutex> g(plan->mu);
+    lct_status st = ensure_device(plan);
+    if (st != LCT_OK) return st;
+    const int64_t chunk = host_chunk(plan) < batch ? host_chunk(plan) : batch;
+    if ((st = ensure_host_state(plan, chunk)) != LCT_OK) return st;
+    const int64_t N = plan->N0;
+    const size_t es = sample_bytes(plan->dtype);
+    const size_t cbytes = (size_t)chunk * (size_t)N * es;
+    char* din[2] = {(char*)plan->hx_buf, (char*)plan->hx_buf + cbytes};
+    char* dout[2] = {(char*)plan->hx_buf + 2 * cbytes, (char*)plan->hx_buf + 3 * cbytes};
+    cudaStream_t s_in = plan->hx_stream[0], s_comp = plan->hx_stream[1], s_out = plan->hx_stream[2];
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // everything after the work already queued on `stream`
+    if (!ok(cudaEventRecord(plan->hx_start, stream)) ||
+        !ok(cudaStreamWaitEvent(s_in, plan->hx_start, 0)) ||
+        !ok(cudaStreamWaitEvent(s_comp, plan->hx_start, 0)) ||
+        !ok(cudaStreamWaitEvent(s_out, plan->hx_start, 0)))
+        return LCT_ERR_CUDA;
+    int64_t k = 0;
+    for (int64_t c0 = 0; c0 < batch; c0 += chunk, ++k) {
+        const int64_t cs = batch - c0 < chunk ? batch - c0 : chunk;
+        const int b = (int)(k & 1);
+        const size_t bytes = (size_t)cs * (size_t)N * es;
+        const size_t hoff = (size_t)c0 * (size_t)N * es;
+        // copy-in: after the compute of chunk k - 2 has read din[b]
+        if (k >= 2 && !ok(cudaStreamWaitEvent(s_in, plan->hx_comp[b], 0))) return LCT_ERR_CUDA;
+        if (!ok(cudaMemcpyAsync(din[b], (const char*)h_in + hoff, bytes, cudaMemcpyHostToDevice, s_in)) ||
+            !ok(cudaEventRecord(plan->hx_in[b], s_in)))
+            return LCT_ERR_CUDA;
+        // compute: after its copy-in and after the copy-out of chunk k - 2
+        if (!ok(cudaStreamWaitEvent(s_comp, plan->hx_in[b], 0))) return LCT_ERR_CUDA;
+        if (k >= 2 && !ok(cudaStreamWaitEvent(s_comp, plan->hx_out[b], 0))) return LCT_ERR_CUDA;
         if (plan->is_batch) {
-            // the plain path assumes contiguous rows
-            for (int64_t s = 0; s < plan->count; ++s)
-                if (plan->desc[s].offset != s * plan->N0) return LCT_ERR_UNSUPPORTED;
+            // descriptors c0.. address samples at offset (c0 + j) N: shift the bases
+            st = execute_locked(plan, plan->d_desc + c0, din[b] - hoff, dout[b] - hoff, cs, s_comp);
+        } else {
+            st = execute_locked(plan, plan->d_desc, din[b], dout[b], cs, s_comp);
         }
-        return run_plain(plan, in, out, batch, desc_step, stream);
+        if (st != LCT_OK) return st;
+        if (!ok(cudaEventRecord(plan->hx_comp[b], s_comp))) return LCT_ERR_CUDA;
+        // copy-out
+        if (!ok(cudaStreamWaitEvent(s_out, plan->hx_comp[b], 0)) ||
+            !ok(cudaMemcpyAsync((char*)h_out + hoff, dout[b], bytes, cudaMemcpyDeviceToHost, s_out)) ||
+            !ok(cudaEventRecord(plan->hx_out[b], s_out)))
+            return LCT_ERR_CUDA;
     }
-    if (plan->prec == LCT_PREC_SPLIT_BF16 || plan->prec == LCT_PREC_SPLIT_FP16 ||
-        plan->prec == LCT_PREC_FP16) {
-        const void* tw = lct_twiddle_table(plan->dtype, log2n);
-        if (log2n >= 5 && !tw) return LCT_ERR_OOM;
-        return from_cuda(lct_launch_split((int)plan->prec, log2n, in, out, plan->d_desc,
-                                          desc_step, batch, tw, tma_aligned(plan, in) ? 1 : 0,
-                                          plan->contiguous ? 1 : 0, plan->d_status, stream));
-    }
-    return run_fused(plan, in, out, batch, desc_step, effective_variant(plan), stream);
+    // `stream` continues after the last copy-out (s_out is in order)
+    if (!ok(cudaEventRecord(plan->hx_out[0], s_out)) ||
+        !ok(cudaStreamWaitEvent(stream, plan->hx_out[0], 0)))
+        return LCT_ERR_CUDA;
+    return LCT_OK;
 }
 
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,

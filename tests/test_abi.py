@@ -146,6 +146,29 @@ def test_precision_selection_host_only():
         rag.destroy()
 
 
+def test_execute_host_validation_without_gpu():
+    """Host-buffer execution needs one N and contiguous signals; the checks
+    come before any device work."""
+    h = np.zeros(4 * 64, dtype=np.complex64)
+    gen = np.array([1.0, 2.0, 0.5, 2.0])
+    gapped = lct.Plan.batch([64] * 3, np.array([gen] * 3), [0, 70, 140], dtype=lct.LCT_C64)
+    ragged = lct.Plan.batch([64, 128], np.array([gen] * 2), [0, 64], dtype=lct.LCT_C64)
+    try:
+        for plan, count in ((gapped, 3), (ragged, 2)):
+            with pytest.raises(lct.LctError) as e:
+                plan.execute_host(h.ctypes.data, h.ctypes.data, count, stream=0)
+            assert e.value.status == 10
+        with pytest.raises(lct.LctError) as e:
+            gapped.execute_host(h.ctypes.data, h.ctypes.data, 2, stream=0)   # batch != count
+        assert e.value.status == 1
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute_host(gapped.handle, 0, h.ctypes.data, 3, stream=0)
+        assert e.value.status == 1
+    finally:
+        gapped.destroy()
+        ragged.destroy()
+
+
 @pytest.mark.parametrize("z", [0.0, 1.5, 2j, complex(float("nan"), 0)])
 def test_frft_bad_z(z):
     with pytest.raises(lct.LctError) as e:
