@@ -46,30 +46,39 @@ __device__ __forceinline__ cpx<R> conj_of(cpx<R> a) { return {a.x, -a.y}; }
 
 // Signals per CTA: interleaved columns (G) or, for rows, enough signals to
 // fill 256 threads.
-template <int L, int G>
+template <int L, int G, int LE = 4>
 struct gen_shape {
-    static constexpr int T = shape<L>::T;
+    static constexpr int T = shape<L, LE>::T;
     static constexpr int SPC = G > 1 ? G : (T >= 256 ? 1 : 256 / T);
     static constexpr int THREADS = T * SPC;
+    // per-signal shared-memory stride: interleaved columns are offset by
+    // 16 / G samples so that the G columns of a half-warp fall on different
+    // banks (a multiple of 16 put them all on the same bank pairs)
+    static constexpr int STR = shape<L, LE>::NP + (G > 1 ? 16 / G : 0);
 };
 
 // 768 resident threads (complex64, <= 85 registers) / 512 (complex128, 128).
-template <int L, class R, int G>
+// LE = 3 (8 samples per thread, complex64 columns): 1024 resident threads
+// at <= 64 registers.
+template <int L, class R, int G, int LE = 4>
 constexpr int gen_min_blocks() {
-    constexpr int per_sm = sizeof(R) == 4 ? 768 : 512;
-    constexpr int b = per_sm / gen_shape<L, G>::THREADS;
+    constexpr int per_sm = sizeof(R) == 4 ? (LE == 3 ? 1024 : 768) : 512;
+    constexpr int b = per_sm / gen_shape<L, G, LE>::THREADS;
     return b < 1 ? 1 : (b > 16 ? 16 : b);
 }
 
-template <int L, class R, int G, bool ADJ, bool GRAD>
-__global__ void __launch_bounds__(gen_shape<L, G>::THREADS, (gen_min_blocks<L, R, G>()))
+// LE: log2 of the samples per thread (4: radix-16 passes with the twiddle
+// table; 3: radix-8 passes with twiddles computed in registers, used for
+// complex64 columns to halve the registers per thread).
+template <int L, class R, int G, bool ADJ, bool GRAD, int LE = 4>
+__global__ void __launch_bounds__(gen_shape<L, G, LE>::THREADS, (gen_min_blocks<L, R, G, LE>()))
 k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
           const lct_desc* __restrict__ desc, int desc_step, int64_t count,
           const cpx<R>* __restrict__ tw, int64_t es, int64_t P, int64_t big,
           const cpx<R>* __restrict__ fwd_out, const cpx<R>* __restrict__ fwd_in,
           double* __restrict__ partial) {
-    using S = shape<L>;
-    using F = gen_shape<L, G>;
+    using S = shape<L, LE>;
+    using F = gen_shape<L, G, LE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
     const int tid = threadIdx.x;
@@ -81,7 +90,7 @@ k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     // rows: unit stride, signal s at s * big; columns: (s / P) * big + (s % P), stride es
     const int64_t base = desc_step ? D.offset : (G > 1 ? (sig / P) * big + (sig % P) : sig * big);
     const int64_t est = G > 1 ? es : 1;
-    cpx<R>* buf = smem + sl * S::NP;
+    cpx<R>* buf = smem + sl * F::STR;
     const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
     const R sc = (R)D.scale;
 
@@ -104,7 +113,7 @@ k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
             v[e] = cmul(x, pre_g<L, R>(D, n, decay));
         }
     }
-    dft_signal<L, ADJ ? 1 : -1>(v, buf, i, tw);
+    dft_signal<L, ADJ ? 1 : -1, LE == 3, LE>(v, buf, i, tw);
     if (active) {
 #pragma unroll
         for (int e = 0; e < S::E; ++e) {
@@ -190,17 +199,17 @@ k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     }
 }
 
-template <int L, class R, int G, bool ADJ, bool GRAD>
+template <int L, class R, int G, bool ADJ, bool GRAD, int LE = 4>
 cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc_step,
                        int64_t count, const void* tw, int64_t es, int64_t P, int64_t big,
                        const void* fwd_out, const void* fwd_in, double* partial,
                        cudaStream_t stream) {
-    using S = shape<L>;
-    using F = gen_shape<L, G>;
-    size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
+    using S = shape<L, LE>;
+    using F = gen_shape<L, G, LE>;
+    size_t smem = S::P > 1 ? (size_t)F::SPC * F::STR * sizeof(cpx<R>) : 0;
     constexpr size_t red_bytes = (size_t)F::THREADS / 32 * (G > 1 ? G : 1) * 3 * sizeof(double) + 64;
     if (GRAD && smem < red_bytes) smem = red_bytes;
-    auto kern = k_xft_gen<L, R, G, ADJ, GRAD>;
+    auto kern = k_xft_gen<L, R, G, ADJ, GRAD, LE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -212,6 +221,24 @@ cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc
         (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw, es, P, big,
         (const cpx<R>*)fwd_out, (const cpx<R>*)fwd_in, partial);
     return cudaGetLastError();
+}
+
+// Complex64 columns: radix-8 engine, 4 interleaved columns per CTA (2 at
+// N = 4096, so that a CTA stays within 1024 threads).
+template <bool ADJ, bool GRAD>
+cudaError_t gen_cols8(int log2n, const void* in, void* out, const lct_desc* desc, int desc_step,
+                      int64_t count, int64_t es, int64_t P, int64_t big, const void* fo,
+                      const void* fi, double* partial, cudaStream_t stream) {
+    switch (log2n) {
+#define LCT_CASE8(L, G)                                                                          \
+    case L:                                                                                      \
+        return launch_gen<L, float, G, ADJ, GRAD, 3>(in, out, desc, desc_step, count, nullptr, es, \
+                                                     P, big, fo, fi, partial, stream);
+        LCT_CASE8(7, 4) LCT_CASE8(8, 4) LCT_CASE8(9, 4) LCT_CASE8(10, 4) LCT_CASE8(11, 4)
+        LCT_CASE8(12, 2)
+#undef LCT_CASE8
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <class R, int G, bool ADJ, bool GRAD>
@@ -315,9 +342,16 @@ cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad
                            const void* fwd_out, const void* fwd_in, double* partial,
                            cudaStream_t stream) {
     if (dtype == 0) {
-        if (cols)
-            return gen_mode<float, 4>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es,
-                                      P, big, fwd_out, fwd_in, partial, stream);
+        if (cols) {
+            if (!adjoint)
+                return gen_cols8<false, false>(log2n, in, out, desc, desc_step, count, es, P, big,
+                                               fwd_out, fwd_in, partial, stream);
+            if (!grad)
+                return gen_cols8<true, false>(log2n, in, out, desc, desc_step, count, es, P, big,
+                                              fwd_out, fwd_in, partial, stream);
+            return gen_cols8<true, true>(log2n, in, out, desc, desc_step, count, es, P, big,
+                                         fwd_out, fwd_in, partial, stream);
+        }
         return gen_mode<float, 1>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es, P,
                                   big, fwd_out, fwd_in, partial, stream);
     }
