@@ -272,6 +272,20 @@ lct_status lct_execute_noalloc(int64_t N, double a, double b, double c, double d
 
 const char* lct_status_string(lct_status status);
 
+/* Multi-GPU sharding of a batch (one process per GPU; the signals are
+ * independent, so no collective is needed on the data path).  Assigns each
+ * of `count` signals to one of `world` ranks by cost, largest first, each to
+ * the currently least-loaded rank (ties: the lowest rank): the cost of a
+ * signal is N log2 N (its DFT), or N when b == 0 (diagonal only, from
+ * abcd_reim in the layout of lct_plan_create_batch; abcd_reim may be NULL:
+ * every signal then costs N log2 N).  Signals of equal cost keep their
+ * order.  Deterministic: every rank computes the same assignment.
+ * owner[s] (count entries) receives the rank of signal s; load (world
+ * entries, may be NULL) each rank's total cost.  Host-only, O(count log
+ * count). */
+lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_reim, int32_t world,
+                         int32_t* owner, double* load);
+
 #ifdef __cplusplus
 }
 #endif

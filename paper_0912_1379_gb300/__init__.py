@@ -64,6 +64,7 @@ def _load():
             "lct_plan_set_precision": [vp, i32],
             "lct_execute": [vp, vp, vp, i64, vp],
             "lct_execute_host": [vp, vp, vp, i64, vp],
+            "lct_partition": [i64, vp, vp, i32, vp, vp],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
@@ -187,6 +188,21 @@ def lct_plan_autotune(plan: int, inp, out, batch: int, stream=None) -> int:
 def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
     _check(_load().lct_execute(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
            "lct_execute")
+
+
+def lct_partition(N, world: int, abcd=None):
+    """Owner rank of every signal (cost-balanced, largest first) and the
+    per-rank loads; see lct_partition in include/lct.h."""
+    n = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
+    owner = np.empty(len(n), dtype=np.int32)
+    load = np.empty(world, dtype=np.float64)
+    p = None
+    if abcd is not None:       # [count, 4] real or complex (a, b, c, d)
+        p = np.ascontiguousarray(np.asarray(abcd, dtype=np.complex128).reshape(len(n), 4)
+                                 .view(np.float64).reshape(-1))
+    _check(_load().lct_partition(len(n), n.ctypes.data, 0 if p is None else p.ctypes.data, world,
+                                 owner.ctypes.data, load.ctypes.data), "lct_partition")
+    return owner, load
 
 
 def lct_execute_host(plan: int, h_in, h_out, batch: int, stream=None) -> None:

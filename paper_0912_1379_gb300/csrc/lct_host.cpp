@@ -20,7 +20,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <numeric>
+#include <queue>
 #include <string>
 #include <mutex>
 #include <new>
@@ -1378,6 +1381,37 @@ lct_status lct2d_plan_destroy(lct2d_plan plan) {
     if (plan->px) lct_plan_destroy(plan->px);
     if (plan->py) lct_plan_destroy(plan->py);
     delete plan;
+    return LCT_OK;
+}
+
+lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_reim, int32_t world,
+                         int32_t* owner, double* load) {
+    if (count < 0 || world < 1 || (count > 0 && (!N || !owner))) return LCT_ERR_ARG;
+    std::vector<double> cost((size_t)count);
+    for (int64_t s = 0; s < count; ++s) {
+        if (ilog2_exact(N[s]) < 0) return LCT_ERR_N;
+        const bool diag = abcd_reim && abcd_reim[8 * s + 2] == 0.0 && abcd_reim[8 * s + 3] == 0.0;
+        cost[(size_t)s] = diag ? (double)N[s] : (double)N[s] * ilog2_exact(N[s]);
+    }
+    std::vector<int64_t> order((size_t)count);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t x, int64_t y) { return cost[(size_t)x] > cost[(size_t)y]; });
+    // least-loaded rank first, then the lowest rank
+    using slot = std::pair<double, int32_t>;
+    std::priority_queue<slot, std::vector<slot>, std::greater<slot>> ranks;
+    for (int32_t r = 0; r < world; ++r) ranks.push({0.0, r});
+    std::vector<double> total((size_t)world, 0.0);
+    for (int64_t s : order) {
+        slot r = ranks.top();
+        ranks.pop();
+        owner[s] = r.second;
+        r.first += cost[(size_t)s];
+        total[(size_t)r.second] = r.first;
+        ranks.push(r);
+    }
+    if (load)
+        for (int32_t r = 0; r < world; ++r) load[r] = total[(size_t)r];
     return LCT_OK;
 }
 
