@@ -272,6 +272,16 @@ lct_status lct_execute_noalloc(int64_t N, double a, double b, double c, double d
 
 const char* lct_status_string(lct_status status);
 
+/* Test support, no counterpart in the paper: runs one kernel whose single
+ * thread waits on purpose for an event that never happens -- which = 0: an
+ * mbarrier phase (the wait of the bulk-copy kernels), 1: a global counter
+ * (the wait of the two-pass kernel) -- bounded by limit_ms milliseconds (at
+ * most 1000), then synchronises `stream`.  Returns LCT_ERR_TIMEOUT when the
+ * wait gave up as designed (the kernel returned normally and the context
+ * stays usable), LCT_OK if it completed, LCT_ERR_ARG for a bad argument,
+ * LCT_ERR_CUDA / LCT_ERR_OOM on runtime errors. */
+lct_status lct_selftest_timeout(int which, double limit_ms, lct_stream_t stream);
+
 /* Multi-GPU sharding of a batch (one process per GPU; the signals are
  * independent, so no collective is needed on the data path).  Assigns each
  * of `count` signals to one of `world` ranks by cost, largest first, each to

@@ -65,6 +65,7 @@ def _load():
             "lct_execute": [vp, vp, vp, i64, vp],
             "lct_execute_host": [vp, vp, vp, i64, vp],
             "lct_partition": [i64, vp, vp, i32, vp, vp],
+            "lct_selftest_timeout": [i32, ctypes.c_double, vp],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
@@ -188,6 +189,12 @@ def lct_plan_autotune(plan: int, inp, out, batch: int, stream=None) -> int:
 def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
     _check(_load().lct_execute(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
            "lct_execute")
+
+
+def lct_selftest_timeout(which: int, limit_ms: float, stream=None) -> int:
+    """Status of one on-purpose bounded device wait (LCT_ERR_TIMEOUT = 9 when
+    it gave up as designed); see include/lct.h."""
+    return int(_load().lct_selftest_timeout(which, limit_ms, _stream_handle(stream)))
 
 
 def lct_partition(N, world: int, abcd=None):

@@ -13,6 +13,7 @@
 // X[k1 + N1 k2] with the post-chirp and scale (GB consecutive k1 per k2).
 #include "xft_engine.cuh"
 #include "xft_chirp.cuh"
+#include "xft_async.cuh"
 
 namespace {
 
@@ -77,33 +78,6 @@ struct pt_shape {
     static constexpr size_t SMEM = ELEMS * sizeof(cpx<R>);
     static_assert(CB >= 1 && RB >= 1, "tile larger than the signal");
 };
-
-__device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
-    int32_t v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Bounded wait for *ctr >= target (thread 0 of the CTA); false on timeout.
-// A timeout anywhere in the launch raises the launch's abort flag, and every
-// later wait then gives up at once, so a fault in the ordering costs one
-// bound, not one per item.
-__device__ __forceinline__ bool wait_geq(const int32_t* ctr, int32_t target, int32_t* abort_flag) {
-    if (ld_acquire(ctr) >= target) return true;
-    if (ld_acquire(abort_flag)) return false;
-    uint64_t t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        __nanosleep(100);
-        if (ld_acquire(ctr) >= target) return true;
-        if ((it & 255) == 255 && ld_acquire(abort_flag)) return false;
-        uint64_t t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > kPtWaitNs) break;
-    }
-    atomicExch(abort_flag, 1);
-    return false;
-}
 
 template <class R>
 __device__ __forceinline__ cpx<R> ld_l2(const cpx<R>* p);
@@ -184,7 +158,7 @@ k_xft_twopass(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, cpx<R>* _
             cpx<R> ws[shape<L1>::E];
             twiddle_powers<shape<L1>::E>(twiddle_exact<R, -1>((n2 * T1) & (N - 1), N), ws);
             // the slot is free once the previous occupant's B tiles have read it
-            if (tid == 0 && round > 0 && !wait_geq(cnt_b + slot, round * RB, abort_flag))
+            if (tid == 0 && round > 0 && !xasync::wait_geq(cnt_b + slot, round * RB, abort_flag, kPtWaitNs))
                 atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
             __syncthreads();
 #pragma unroll
@@ -197,7 +171,7 @@ k_xft_twopass(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, cpx<R>* _
             }
         } else {
             const int r = tid / T2, i = tid % T2;
-            if (tid == 0 && !wait_geq(cnt_a + slot, (round + 1) * CB, abort_flag))
+            if (tid == 0 && !xasync::wait_geq(cnt_a + slot, (round + 1) * CB, abort_flag, kPtWaitNs))
                 atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
             __syncthreads();
             const int k1b = tile * GB;

@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <complex>
@@ -497,6 +498,15 @@ lct_status ensure_device(lct_plan p) {
     return LCT_OK;
 }
 
+// NVTX range over an entry point (visible in Nsight timelines; costs a
+// call into the NVTX stub when no tool is attached).
+struct trace_range {
+    explicit trace_range(const char* name) { nvtxRangePushA(name); }
+    ~trace_range() { nvtxRangePop(); }
+    trace_range(const trace_range&) = delete;
+    trace_range& operator=(const trace_range&) = delete;
+};
+
 lct_status check_ptr(const void* ptr, lct_dtype dt) {
     if (!ptr) return LCT_ERR_ARG;
     uintptr_t align = dt == LCT_C64 ? 8 : 16;
@@ -960,6 +970,7 @@ extern "C" {
 
 lct_status lct_plan_create(lct_plan* out, int64_t N, double a, double b, double c, double d,
                            lct_dtype dtype) {
+    trace_range trace("lct_plan_create");
     double p[8] = {a, 0.0, b, 0.0, c, 0.0, d, 0.0};
     return new_plan(out, dtype, 1, &N, p, nullptr, false);
 }
@@ -973,6 +984,7 @@ lct_status lct_plan_create_complex(lct_plan* out, int64_t N, const double abcd_r
 lct_status lct_plan_create_batch(lct_plan* out, int64_t count, const int64_t* N,
                                  const double* abcd_reim, const int64_t* offsets,
                                  lct_dtype dtype) {
+    trace_range trace("lct_plan_create_batch");
     if (!N || !abcd_reim || !offsets) return LCT_ERR_ARG;
     return new_plan(out, dtype, count, N, abcd_reim, offsets, true);
 }
@@ -1016,6 +1028,7 @@ lct_status lct_plan_get_variant(lct_plan plan, int* variant) {
 
 lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t batch,
                              lct_stream_t stream_) {
+    trace_range trace("lct_plan_autotune");
     if (!plan) return LCT_ERR_ARG;
     if (plan->prec != LCT_PREC_NATIVE || plan->N0 == 0 || plan->desc[0].kind != LCT_KIND_XFT) {
         plan->variant = 0;
@@ -1076,6 +1089,7 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
 
 lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                        lct_stream_t stream_) {
+    trace_range trace("lct_execute");
     if (!plan) return LCT_ERR_ARG;
     if (batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
@@ -1092,6 +1106,7 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
 
 lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
                             lct_stream_t stream_) {
+    trace_range trace("lct_execute_host");
     if (!plan || !h_in || !h_out || batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
@@ -1153,6 +1168,7 @@ lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_
 
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                         int64_t batch, lct_dtype dtype, lct_stream_t stream) {
+    trace_range trace("frft_execute");
     cplx z(z_re, z_im);
     double az = std::abs(z);
     if (!std::isfinite(az) || az == 0.0 || az > 1.0 + 1e-15) return LCT_ERR_ARG;
@@ -1266,6 +1282,7 @@ lct_status lct_plan_destroy(lct_plan plan) {
 
 lct_status lct_backward(lct_plan plan, const void* grad_out, const void* in, const void* out,
                         void* grad_in, double* grad_abd, int64_t batch, lct_stream_t stream_) {
+    trace_range trace("lct_backward");
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
@@ -1325,6 +1342,7 @@ lct_status lct2d_plan_create(lct2d_plan* out, int64_t ny, int64_t nx, const doub
 
 lct_status lct2d_execute(lct2d_plan plan, const void* in, void* mid, void* out, int64_t batch,
                          lct_stream_t stream_) {
+    trace_range trace("lct2d_execute");
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
     lct_status st = check_ptr(mid, plan->dtype);
@@ -1350,6 +1368,7 @@ lct_status lct2d_execute(lct2d_plan plan, const void* in, void* mid, void* out, 
 lct_status lct2d_backward(lct2d_plan plan, const void* grad_out, const void* in, const void* mid,
                           const void* out, void* grad_mid, void* grad_in, double* grad_abd,
                           int64_t batch, lct_stream_t stream_) {
+    trace_range trace("lct2d_backward");
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
     const void* ptrs[4] = {grad_out, grad_mid, grad_in, grad_abd ? mid : grad_out};
@@ -1382,6 +1401,23 @@ lct_status lct2d_plan_destroy(lct2d_plan plan) {
     if (plan->py) lct_plan_destroy(plan->py);
     delete plan;
     return LCT_OK;
+}
+
+lct_status lct_selftest_timeout(int which, double limit_ms, lct_stream_t stream_) {
+    if ((which != 0 && which != 1) || !(limit_ms > 0.0) || limit_ms > 1000.0) return LCT_ERR_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int32_t* word = nullptr;
+    if (cudaMalloc(&word, 4 * sizeof(int32_t)) != cudaSuccess) return LCT_ERR_OOM;
+    lct_status st = LCT_OK;
+    int32_t result = -1;
+    if (cudaMemsetAsync(word, 0, 4 * sizeof(int32_t), stream) != cudaSuccess ||
+        lct_launch_selftest_wait(which, (uint64_t)(limit_ms * 1e6), word, stream) != cudaSuccess ||
+        cudaMemcpyAsync(&result, word, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        st = LCT_ERR_CUDA;
+    cudaFree(word);
+    if (st != LCT_OK) return st;
+    return result == LCT_DEV_TIMEOUT ? LCT_ERR_TIMEOUT : (result == LCT_DEV_OK ? LCT_OK : LCT_ERR_CUDA);
 }
 
 lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_reim, int32_t world,

@@ -127,6 +127,11 @@ cudaError_t lct_launch_twopass(int dtype, int log2n, const void* in, void* out, 
                                const int32_t* idx, int32_t* status, const void* tw1,
                                const void* tw2, cudaStream_t stream);
 
+// Self-test of the bounded waits (k_selftest.cu): word[0..2] zeroed device
+// int32; which 0 = mbarrier wait, 1 = counter wait.
+cudaError_t lct_launch_selftest_wait(int which, uint64_t limit_ns, int32_t* word,
+                                     cudaStream_t stream);
+
 // Split-precision XFT on the tensor cores (complex64, N = 16 .. 4096; a CTA
 // transforms 4096/N signals).  mode: 1 = split BF16 (three products),
 // 2 = split FP16 (three products, per-signal power-of-two scaling), 3 = FP16

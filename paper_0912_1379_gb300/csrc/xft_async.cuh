@@ -74,4 +74,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     return false;
 }
 
+__device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait for *ctr >= target (one thread); false on timeout after
+// `limit_ns` nanoseconds (at most 2^26 polls).  A timeout raises *abort_flag,
+// and every later wait that sees the flag gives up at once, so a fault in an
+// ordering costs one bound, not one per waiter.
+__device__ __forceinline__ bool wait_geq(const int32_t* ctr, int32_t target, int32_t* abort_flag,
+                                         uint64_t limit_ns) {
+    if (ld_acquire(ctr) >= target) return true;
+    if (ld_acquire(abort_flag)) return false;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        __nanosleep(100);
+        if (ld_acquire(ctr) >= target) return true;
+        if ((it & 255) == 255 && ld_acquire(abort_flag)) return false;
+        if (globaltimer_ns() - t0 > limit_ns) break;
+    }
+    atomicExch(abort_flag, 1);
+    return false;
+}
+
 }  // namespace xasync

@@ -169,6 +169,11 @@ def test_execute_host_validation_without_gpu():
         ragged.destroy()
 
 
+def test_selftest_timeout_arguments_without_gpu():
+    for which, ms in [(2, 1.0), (-1, 1.0), (0, 0.0), (1, 2000.0), (0, float("nan"))]:
+        assert lct.lct_selftest_timeout(which, ms, stream=0) == 1
+
+
 @pytest.mark.parametrize("z", [0.0, 1.5, 2j, complex(float("nan"), 0)])
 def test_frft_bad_z(z):
     with pytest.raises(lct.LctError) as e:
