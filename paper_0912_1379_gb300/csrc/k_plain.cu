@@ -44,30 +44,34 @@ __global__ void k_diag(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     }
 }
 
-// b = 0 over a ragged list of descriptors, one CTA per signal.
+// b = 0 over the ragged list of every diagonal signal of a batch, one launch:
+// chunk c = {pos, start, log2n, nsig} covers elements start .. start + 2047
+// of signal idx[pos] (nsig == 1, N >= 2048) or the nsig whole signals
+// idx[pos .. pos + nsig - 1] of equal N (nsig N <= 2048).  Mismatching
+// descriptors are skipped and flagged.
 template <class R>
-__global__ void k_diag_ragged(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+__global__ void k_diag_chunks(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
                               const lct_desc* __restrict__ desc, const int32_t* __restrict__ idx,
-                              int64_t count, int32_t* __restrict__ status) {
-    for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
-        const lct_desc& D = desc[idx[s]];
-        if (D.kind != LCT_KIND_DIAG || D.log2n < 1 || D.log2n > 16 || D.offset < 0) {
-            if (threadIdx.x == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
-            continue;
-        }
-        const int N = 1 << D.log2n;
-        if constexpr (sizeof(R) == 4) {
-            // complex64: FP32 arithmetic on the exact 32-bit turn fraction
-            const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
-            const float sc = (float)D.scale;
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                const uint32_t m2 = m_squared(n, N);
-                cpx<float> w = expi_turn32<true>(phase32(D.out_hi, m2) + off);
-                out[D.offset + n] = cscale(cmul(in[D.offset + n], w), sc);
+                              const int4* __restrict__ chunks, int64_t nchunks,
+                              int32_t* __restrict__ status) {
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int4 ch = chunks[c];
+        const int L = ch.z, N = 1 << L;
+        const int len = ch.w > 1 ? (ch.w << L) : min(N - ch.y, kDiagChunk);
+        for (int e = threadIdx.x; e < len; e += blockDim.x) {
+            const int j = ch.w > 1 ? (e >> L) : 0;
+            const int n = ch.w > 1 ? (e & (N - 1)) : ch.y + e;
+            const lct_desc& D = desc[idx[ch.x + j]];
+            if (D.kind != LCT_KIND_DIAG || D.log2n != L || D.offset < 0) {
+                if (n == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+                continue;
             }
-        } else {
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                const uint32_t m2 = m_squared(n, N);
+            const uint32_t m2 = m_squared(n, N);
+            if constexpr (sizeof(R) == 4) {
+                const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
+                cpx<float> w = expi_turn32<true>(phase32(D.out_hi, m2) + off);
+                out[D.offset + n] = cscale(cmul(in[D.offset + n], w), (float)D.scale);
+            } else {
                 cpx<double> w = expi_turn64(phase64(D.out_hi, D.out_lo, m2) + D.out_c);
                 cpx<double> g = cscale(cmul(load_c128(in, D.offset + n), w), D.scale);
                 out[D.offset + n] = {(R)g.x, (R)g.y};
@@ -141,17 +145,22 @@ cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,
     return cudaGetLastError();
 }
 
-cudaError_t lct_launch_diag_ragged(int dtype, const void* in, void* out, const lct_desc* desc,
-                                   const int32_t* idx, int64_t count, int32_t* status,
-                                   cudaStream_t stream) {
-    if (count <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)(count < 152 * 8 ? count : 152 * 8);
+cudaError_t lct_launch_diag_chunks(int dtype, const void* in, void* out, const lct_desc* desc,
+                                   const int32_t* idx, const int32_t* chunks, int64_t nchunks,
+                                   int32_t* status, cudaStream_t stream) {
+    if (nchunks <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t cap = (int64_t)sms * 8;
+    const unsigned grid = (unsigned)(nchunks < cap ? nchunks : cap);
     if (dtype == 0)
-        k_diag_ragged<float><<<grid, 256, 0, stream>>>((const cpx<float>*)in, (cpx<float>*)out,
-                                                       desc, idx, count, status);
+        k_diag_chunks<float><<<grid, 256, 0, stream>>>((const cpx<float>*)in, (cpx<float>*)out,
+                                                       desc, idx, (const int4*)chunks, nchunks, status);
     else
-        k_diag_ragged<double><<<grid, 256, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out,
-                                                        desc, idx, count, status);
+        k_diag_chunks<double><<<grid, 256, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out,
+                                                        desc, idx, (const int4*)chunks, nchunks, status);
     return cudaGetLastError();
 }
 

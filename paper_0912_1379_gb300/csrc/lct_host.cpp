@@ -309,11 +309,20 @@ struct lct_plan_s {
     int variant = -1;               // -1: not chosen (cache or default 0)
     // ragged execution (mixed N or kinds): groups of equal (N, kind), largest
     // N first, each an index list into desc; run as one CUDA graph
-    struct group { int log2n, kind; int64_t count, idx_off; int64_t tp_off = -1; };
+    // kind LCT_KIND_DIAG: one group for every diagonal signal (log2n = -1),
+    // its idx list ordered by N, run through the chunk list chunks[chunk_off ..]
+    struct group {
+        int log2n, kind;
+        int64_t count, idx_off;
+        int64_t tp_off = -1;
+        int64_t chunk_off = 0, nchunks = 0;
+    };
     bool ragged = false;
     std::vector<group> groups;
     std::vector<int32_t> idx;       // concatenated index lists
     int32_t* d_idx = nullptr;
+    std::vector<int32_t> chunks;    // diagonal-group chunks, 4 int32 each
+    int32_t* d_chunks = nullptr;
     static constexpr int kBranches = 4;
     cudaStream_t cap = nullptr;
     cudaStream_t side[kBranches] = {};
@@ -448,6 +457,8 @@ void release_device(lct_plan p) {
     p->tp_bytes = 0;
     cudaFree(p->d_idx);
     p->d_idx = nullptr;
+    cudaFree(p->d_chunks);
+    p->d_chunks = nullptr;
     cudaFree(p->d_coef);
     cudaFree(p->d_partial);
     p->d_coef = nullptr;
@@ -491,6 +502,17 @@ lct_status ensure_device(lct_plan p) {
             return LCT_ERR_OOM;
         }
         if (cudaMemcpy(p->d_idx, p->idx.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) {
+            release_device(p);
+            return LCT_ERR_CUDA;
+        }
+    }
+    if (p->ragged && !p->chunks.empty()) {
+        const size_t cb = sizeof(int32_t) * p->chunks.size();
+        if (cudaMalloc(&p->d_chunks, cb) != cudaSuccess) {
+            release_device(p);
+            return LCT_ERR_OOM;
+        }
+        if (cudaMemcpy(p->d_chunks, p->chunks.data(), cb, cudaMemcpyHostToDevice) != cudaSuccess) {
             release_device(p);
             return LCT_ERR_CUDA;
         }
@@ -554,7 +576,33 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
             const lct_desc& D = p->desc[s];
             by[{D.log2n, D.kind}].push_back((int32_t)s);
         }
+        lct_plan_s::group diag;
+        diag.log2n = -1;
+        diag.kind = LCT_KIND_DIAG;
+        diag.count = 0;
+        std::vector<int32_t> diag_idx;
         for (auto& kv : by) {
+            if (kv.first.second == LCT_KIND_DIAG) {
+                // chunks of kDiagChunk elements, or whole small signals packed
+                const int L = kv.first.first;
+                const int64_t n = (int64_t)1 << L;
+                const int64_t pos0 = (int64_t)diag_idx.size();
+                const int64_t m = (int64_t)kv.second.size();
+                if (n >= kDiagChunk) {
+                    for (int64_t j = 0; j < m; ++j)
+                        for (int64_t st = 0; st < n; st += kDiagChunk)
+                            p->chunks.insert(p->chunks.end(),
+                                             {(int32_t)(pos0 + j), (int32_t)st, L, 1});
+                } else {
+                    const int64_t per = kDiagChunk / n;
+                    for (int64_t j = 0; j < m; j += per)
+                        p->chunks.insert(p->chunks.end(),
+                                         {(int32_t)(pos0 + j), 0, L,
+                                          (int32_t)(m - j < per ? m - j : per)});
+                }
+                diag_idx.insert(diag_idx.end(), kv.second.begin(), kv.second.end());
+                continue;
+            }
             lct_plan_s::group g;
             g.log2n = kv.first.first;
             g.kind = kv.first.second;
@@ -562,6 +610,14 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
             g.idx_off = (int64_t)p->idx.size();
             p->idx.insert(p->idx.end(), kv.second.begin(), kv.second.end());
             p->groups.push_back(g);
+        }
+        if (!diag_idx.empty()) {
+            diag.count = (int64_t)diag_idx.size();
+            diag.idx_off = (int64_t)p->idx.size();
+            diag.chunk_off = 0;
+            diag.nchunks = (int64_t)(p->chunks.size() / 4);
+            p->idx.insert(p->idx.end(), diag_idx.begin(), diag_idx.end());
+            p->groups.push_back(diag);
         }
     }
     *out = p;
@@ -728,8 +784,9 @@ lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, 
                         cudaStream_t stream) {
     const int32_t* idx = p->d_idx + g.idx_off;
     if (g.kind == LCT_KIND_DIAG)
-        return from_cuda(lct_launch_diag(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count, idx,
-                                         p->d_status, stream));
+        return from_cuda(lct_launch_diag_chunks(p->dtype, in, out, p->d_desc, idx,
+                                                p->d_chunks + 4 * g.chunk_off, g.nchunks,
+                                                p->d_status, stream));
     const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
     const bool single = lct_fused_supported(p->dtype, g.log2n);
     const int v = tune_lookup(p->dtype, g.log2n);

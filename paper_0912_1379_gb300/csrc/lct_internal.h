@@ -151,11 +151,15 @@ cudaError_t lct_launch_diag(int dtype, int log2n, const void* in, void* out,
                             const lct_desc* desc, int desc_step, int64_t count,
                             const int32_t* idx, int32_t* status, cudaStream_t stream);
 
-// Diagonal branch (b == 0) over a ragged list: descriptors idx[0..count),
-// any N; one CTA per signal.  Mismatching descriptors set LCT_DEV_BAD_DESC.
-cudaError_t lct_launch_diag_ragged(int dtype, const void* in, void* out, const lct_desc* desc,
-                                   const int32_t* idx, int64_t count, int32_t* status,
-                                   cudaStream_t stream);
+// Diagonal branch (b == 0) for every diagonal signal of a ragged batch in
+// one launch.  chunks: nchunks int32 quadruples {pos, start, log2n, nsig}
+// (16-byte aligned): elements start .. start + kDiagChunk - 1 of signal
+// idx[pos] (nsig == 1) or the nsig whole signals idx[pos ..] of equal N
+// (nsig N <= kDiagChunk).  Mismatching descriptors set LCT_DEV_BAD_DESC.
+constexpr int kDiagChunk = 2048;
+cudaError_t lct_launch_diag_chunks(int dtype, const void* in, void* out, const lct_desc* desc,
+                                   const int32_t* idx, const int32_t* chunks, int64_t nchunks,
+                                   int32_t* status, cudaStream_t stream);
 
 // General single-CTA kernel (k_general.cu): forward or adjoint, rows
 // (cols = 0) or interleaved columns (cols = 1), optional gradient sums
