@@ -276,9 +276,11 @@ cudaError_t gen_mode(int log2n, bool adj, bool grad, const void* in, void* out,
 // (cA_a, cA_b, cR_b, cG_b, cG_d).  shared != 0: one parameter set for all
 // signals, the sums are added first and grad has 3 entries.
 constexpr int kFinalizeThreads = 1024;
+constexpr int kFinalizeBlocks = 64;
 
 __global__ void k_grad_finalize(const double* __restrict__ partial, const double* __restrict__ coef,
-                                int coef_step, int64_t count, int shared, double* __restrict__ grad) {
+                                int coef_step, int64_t count, int shared, double* __restrict__ grad,
+                                double* __restrict__ scratch) {
     if (!shared) {
         for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < count;
              s += (int64_t)gridDim.x * blockDim.x) {
@@ -290,12 +292,18 @@ __global__ void k_grad_finalize(const double* __restrict__ partial, const double
         }
         return;
     }
-    // one CTA of kFinalizeThreads threads, four independent accumulation
-    // chains per thread, then a tree over the CTA (fixed order: deterministic)
+    // Shared parameters: CTA b sums its slice of the signals (four chains per
+    // thread, then a tree), stores the slice total in scratch[3 b ..]; the
+    // last CTA to finish adds the slice totals in slice order (deterministic)
+    // and resets the ticket counter for the next launch.
     __shared__ double red[3][kFinalizeThreads];
+    __shared__ bool last;
+    const int64_t slice = (count + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = blockIdx.x * slice;
+    const int64_t s1 = s0 + slice < count ? s0 + slice : count;
     double a[4] = {0, 0, 0, 0}, r[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
-    int64_t s = threadIdx.x;
-    for (; s + 3 * (int64_t)blockDim.x < count; s += 4 * (int64_t)blockDim.x) {
+    int64_t s = s0 + threadIdx.x;
+    for (; s + 3 * (int64_t)blockDim.x < s1; s += 4 * (int64_t)blockDim.x) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int64_t t = s + u * (int64_t)blockDim.x;
@@ -304,7 +312,7 @@ __global__ void k_grad_finalize(const double* __restrict__ partial, const double
             g[u] += partial[3 * t + 2];
         }
     }
-    for (; s < count; s += blockDim.x) {
+    for (; s < s1; s += blockDim.x) {
         a[0] += partial[3 * s];
         r[0] += partial[3 * s + 1];
         g[0] += partial[3 * s + 2];
@@ -318,11 +326,26 @@ __global__ void k_grad_finalize(const double* __restrict__ partial, const double
             for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
         __syncthreads();
     }
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + 3 * kFinalizeBlocks);
     if (threadIdx.x == 0) {
-        const double SA = red[0][0], SR = red[1][0], SG = red[2][0];
+        for (int q = 0; q < 3; ++q) scratch[3 * blockIdx.x + q] = red[q][0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double* v = scratch;
+        double SA = 0, SR = 0, SG = 0;
+        for (unsigned int b = 0; b < gridDim.x; ++b) {
+            SA += v[3 * b];
+            SR += v[3 * b + 1];
+            SG += v[3 * b + 2];
+        }
         grad[0] = coef[0] * SA;
         grad[1] = coef[1] * SA + coef[2] * SR + coef[3] * SG;
         grad[2] = coef[4] * SG;
+        atomicExch(ticket, 0u);
     }
 }
 
@@ -363,11 +386,19 @@ cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad
 }
 
 cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, int coef_step,
-                                     int64_t count, int shared, double* grad, cudaStream_t stream) {
-    if (shared)
-        k_grad_finalize<<<1, kFinalizeThreads, 0, stream>>>(partial, coef, coef_step, count, 1, grad);
-    else
+                                     int64_t count, int shared, double* grad, double* scratch,
+                                     cudaStream_t stream) {
+    if (shared) {
+        int64_t blocks = (count + 4095) / 4096;                 // at least 4096 signals per CTA
+        if (blocks > kFinalizeBlocks) blocks = kFinalizeBlocks;
+        if (blocks < 1) blocks = 1;
+        k_grad_finalize<<<(unsigned)blocks, kFinalizeThreads, 0, stream>>>(
+            partial, coef, coef_step, count, 1, grad, scratch);
+    } else {
         k_grad_finalize<<<(unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096), 256, 0,
-                          stream>>>(partial, coef, coef_step, count, 0, grad);
+                          stream>>>(partial, coef, coef_step, count, 0, grad, scratch);
+    }
     return cudaGetLastError();
 }
+
+size_t lct_grad_finalize_scratch_bytes() { return (3 * kFinalizeBlocks + 1) * sizeof(double); }

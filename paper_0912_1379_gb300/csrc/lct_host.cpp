@@ -901,10 +901,13 @@ lct_status ensure_grad_state(lct_plan p, int64_t batch) {
             return LCT_ERR_CUDA;
     }
     if (batch > p->partial_count) {
+        // per-signal sums, then the finalize scratch (zeroed once)
         cudaFree(p->d_partial);
         p->d_partial = nullptr;
         p->partial_count = 0;
-        if (cudaMalloc(&p->d_partial, sizeof(double) * 3 * batch) != cudaSuccess) return LCT_ERR_OOM;
+        const size_t bytes = sizeof(double) * 3 * batch + lct_grad_finalize_scratch_bytes();
+        if (cudaMalloc(&p->d_partial, bytes) != cudaSuccess) return LCT_ERR_OOM;
+        if (cudaMemset(p->d_partial, 0, bytes) != cudaSuccess) return LCT_ERR_CUDA;
         p->partial_count = batch;
     }
     return LCT_OK;
@@ -937,7 +940,8 @@ lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G,
                                              do_grad ? p->d_partial : nullptr, stream));
     if (st != LCT_OK || !do_grad) return st;
     return from_cuda(lct_launch_grad_finalize(p->d_partial, p->d_coef, desc_step, batch,
-                                              p->is_batch ? 0 : 1, grad, stream));
+                                              p->is_batch ? 0 : 1, grad,
+                                              p->d_partial + 3 * p->partial_count, stream));
 }
 
 lct_status run_ragged(lct_plan p, const void* in, void* out, cudaStream_t stream) {

@@ -175,7 +175,11 @@ cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad
 // per signal (coef_step 1) or shared (coef_step 0); shared != 0 sums over
 // the signals into grad[0..2].
 cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, int coef_step,
-                                     int64_t count, int shared, double* grad, cudaStream_t stream);
+                                     int64_t count, int shared, double* grad, double* scratch,
+                                     cudaStream_t stream);
+// Bytes of the finalize scratch (slice totals and a ticket counter that must
+// be zero before the first launch; the kernel leaves it zero).
+size_t lct_grad_finalize_scratch_bytes();
 
 // Plain FP64 baseline pieces.  work: complex128 [count][N].
 cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,
