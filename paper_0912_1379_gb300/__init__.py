@@ -66,6 +66,7 @@ def _load():
             "lct_execute_host": [vp, vp, vp, i64, vp],
             "lct_partition": [i64, vp, vp, i32, vp, vp],
             "lct_selftest_timeout": [i32, ctypes.c_double, vp],
+            "lct_set_debug": [i32],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
@@ -189,6 +190,12 @@ def lct_plan_autotune(plan: int, inp, out, batch: int, stream=None) -> int:
 def lct_execute(plan: int, inp, out, batch: int, stream=None) -> None:
     _check(_load().lct_execute(plan, _ptr(inp), _ptr(out), batch, _stream_handle(stream)),
            "lct_execute")
+
+
+def lct_set_debug(on: bool) -> None:
+    """Debug mode: synchronous output scan and status check after each
+    lct_execute (see include/lct.h)."""
+    _check(_load().lct_set_debug(1 if on else 0), "lct_set_debug")
 
 
 def lct_selftest_timeout(which: int, limit_ms: float, stream=None) -> int:

@@ -80,6 +80,22 @@ __global__ void k_diag_chunks(const cpx<R>* __restrict__ in, cpx<R>* __restrict_
     }
 }
 
+// Debug scan for NaN / infinite samples, one CTA per signal (grid-stride).
+template <class R>
+__global__ void k_scan(const cpx<R>* __restrict__ out, const lct_desc* __restrict__ desc,
+                       int desc_step, int64_t count, int log2n, int32_t* __restrict__ status) {
+    for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
+        const int L = desc_step ? desc[s].log2n : log2n;
+        const int64_t base = desc_step ? desc[s].offset : s << log2n;
+        bool bad = false;
+        for (int n = threadIdx.x; n < (1 << L); n += blockDim.x) {
+            const cpx<R> v = out[base + n];
+            bad |= !isfinite(v.x) || !isfinite(v.y);
+        }
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_NONFINITE);
+    }
+}
+
 // plain path, step 1: u_k = e^{2 pi i [phi_in m^2 + (N-1)k/(2N)]} e^{-decay m^2} f_k (FP64)
 template <class R>
 __global__ void k_plain_pre(const cpx<R>* __restrict__ in, cpx<double>* __restrict__ work,
@@ -161,6 +177,19 @@ cudaError_t lct_launch_diag_chunks(int dtype, const void* in, void* out, const l
     else
         k_diag_chunks<double><<<grid, 256, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out,
                                                         desc, idx, (const int4*)chunks, nchunks, status);
+    return cudaGetLastError();
+}
+
+cudaError_t lct_launch_scan(int dtype, const void* out, const lct_desc* desc, int desc_step,
+                            int64_t count, int log2n, int32_t* status, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(count < 4096 ? count : 4096);
+    if (dtype == 0)
+        k_scan<float><<<grid, 256, 0, stream>>>((const cpx<float>*)out, desc, desc_step, count,
+                                                log2n, status);
+    else
+        k_scan<double><<<grid, 256, 0, stream>>>((const cpx<double>*)out, desc, desc_step, count,
+                                                 log2n, status);
     return cudaGetLastError();
 }
 

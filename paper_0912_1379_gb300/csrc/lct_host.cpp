@@ -22,6 +22,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <numeric>
 #include <queue>
@@ -529,6 +530,22 @@ struct trace_range {
     trace_range& operator=(const trace_range&) = delete;
 };
 
+// Debug mode (LCT_DEBUG=1 in the environment, or lct_set_debug): every
+// lct_execute / lct_backward synchronises its stream, scans the outputs for
+// non-finite samples and reports the device status word.
+std::atomic<int> g_debug{-1};
+bool debug_on() {
+    int v = g_debug.load();
+    if (v < 0) {
+        const char* e = std::getenv("LCT_DEBUG");
+        v = (e && e[0] && e[0] != '0') ? 1 : 0;
+        int expect = -1;
+        g_debug.compare_exchange_strong(expect, v);
+        v = g_debug.load();
+    }
+    return v == 1;
+}
+
 lct_status check_ptr(const void* ptr, lct_dtype dt) {
     if (!ptr) return LCT_ERR_ARG;
     uintptr_t align = dt == LCT_C64 ? 8 : 16;
@@ -989,6 +1006,24 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
     return run_fused(plan, in, out, batch, desc_step, effective_variant(plan), stream);
 }
 
+// Debug mode: scan `count` output signals laid out as the plan's (batch plans:
+// by descriptor; others: contiguous rows of N0), wait, report and clear the
+// device status word.
+lct_status debug_check(lct_plan plan, const void* out, int64_t count, cudaStream_t stream) {
+    const int desc_step = plan->is_batch ? 1 : 0;
+    const int log2n = plan->desc[0].log2n;
+    if (lct_launch_scan(plan->dtype, out, plan->d_desc, desc_step, count, log2n, plan->d_status,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return LCT_ERR_CUDA;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, plan->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LCT_ERR_CUDA;
+    if (v == LCT_DEV_OK) return LCT_OK;
+    cudaMemset(plan->d_status, 0, sizeof(int32_t));
+    return v == LCT_DEV_TIMEOUT ? LCT_ERR_TIMEOUT : LCT_ERR_DEVICE;
+}
+
 // Host-buffer execution ----------------------------------------------------
 // Signals per chunk: about 32 MiB of samples, at least one signal (measured
 // on GB300 with 512 MiB each way: 16 MiB 3.62 ms, 32 MiB 3.46 ms, 64 MiB
@@ -1162,7 +1197,9 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
     std::lock_guard<std::mutex> g(plan->mu);
     st = ensure_device(plan);
     if (st != LCT_OK) return st;
-    return execute_locked(plan, plan->d_desc, in, out, batch, (cudaStream_t)stream_);
+    st = execute_locked(plan, plan->d_desc, in, out, batch, (cudaStream_t)stream_);
+    if (st == LCT_OK && debug_on()) st = debug_check(plan, out, batch, (cudaStream_t)stream_);
+    return st;
 }
 
 lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
@@ -1461,6 +1498,11 @@ lct_status lct2d_plan_destroy(lct2d_plan plan) {
     if (plan->px) lct_plan_destroy(plan->px);
     if (plan->py) lct_plan_destroy(plan->py);
     delete plan;
+    return LCT_OK;
+}
+
+lct_status lct_set_debug(int on) {
+    g_debug.store(on ? 1 : 0);
     return LCT_OK;
 }
 

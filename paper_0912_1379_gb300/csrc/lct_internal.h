@@ -41,7 +41,7 @@ struct __align__(16) lct_desc {
 static_assert(sizeof(lct_desc) == 80, "descriptor layout");
 
 // Device status word values (first error wins).
-enum { LCT_DEV_OK = 0, LCT_DEV_BAD_DESC = 1, LCT_DEV_TIMEOUT = 2 };
+enum { LCT_DEV_OK = 0, LCT_DEV_BAD_DESC = 1, LCT_DEV_TIMEOUT = 2, LCT_DEV_NONFINITE = 3 };
 
 // Host: the descriptor of one N-point signal with parameters
 // p = {a_re, a_im, b_re, b_im, c_re, c_im, d_re, d_im} (validates like
@@ -180,6 +180,13 @@ cudaError_t lct_launch_grad_finalize(const double* partial, const double* coef, 
 // Bytes of the finalize scratch (slice totals and a ticket counter that must
 // be zero before the first launch; the kernel leaves it zero).
 size_t lct_grad_finalize_scratch_bytes();
+
+// Debug scan: records LCT_DEV_NONFINITE in *status if any sample of the
+// `count` output signals is NaN or infinite.  desc_step = 0: signal s is
+// elements [s N, (s + 1) N) with N = 2^log2n; desc_step = 1: desc[s].offset
+// and desc[s].log2n.
+cudaError_t lct_launch_scan(int dtype, const void* out, const lct_desc* desc, int desc_step,
+                            int64_t count, int log2n, int32_t* status, cudaStream_t stream);
 
 // Plain FP64 baseline pieces.  work: complex128 [count][N].
 cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,

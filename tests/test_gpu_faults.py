@@ -43,3 +43,36 @@ def test_bounded_wait_times_out_and_context_survives(which):
     finally:
         p.destroy()
     assert rel_l2(G, O.lct(f.astype(np.complex128), params)).max() < 1e-5
+
+
+@pytest.mark.parametrize("batch_plan", [False, True])
+def test_debug_mode_flags_nonfinite_output(batch_plan):
+    """LCT_DEBUG / lct_set_debug: a NaN in the input reaches the output and
+    lct_execute reports LCT_ERR_DEVICE (8); finite data passes; off again,
+    nothing is checked."""
+    N, count = 256, 8
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=4, dtype=np.complex64)
+    if batch_plan:
+        p = lct.Plan.batch([N] * count, params, np.arange(count) * N)
+    else:
+        p = lct.Plan.create(N, *params[0])
+    bad = f.copy()
+    bad[3, 17] = np.nan
+    try:
+        lct.lct_set_debug(True)
+        xin = torch.from_numpy(f).cuda()
+        out = torch.empty_like(xin)
+        lct.lct_execute(p.handle, xin, out, count)              # finite: no error
+        xbad = torch.from_numpy(bad).cuda()
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_execute(p.handle, xbad, out, count)
+        assert e.value.status == 8
+        assert lct.lct_device_status(p.handle) == 0             # the word was cleared
+        lct.lct_set_debug(False)
+        lct.lct_execute(p.handle, xbad, out, count)             # not checked when off
+        torch.cuda.synchronize()
+        assert not np.isfinite(out.cpu().numpy()[3]).all()
+    finally:
+        lct.lct_set_debug(False)
+        p.destroy()
