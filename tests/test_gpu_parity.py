@@ -374,6 +374,50 @@ def test_ragged_mixed_sizes_and_kinds():
     assert np.all(G[mask] == 0)
 
 
+SMALL_SPECS = [
+    (1, "lct", (0.4, 1.3, (0.4 * -0.7 - 1) / 1.3, -0.7)),
+    (2, "frft", 0.6 * np.exp(1.1j)),
+    (3, "lct", (0.0, 1.0, -1.0, 0.0)),
+    (1, "b0", (1 / 1.4, 0.0, 0.7, 1.4)),
+    (4, "lct", (-1.2, -0.5, (-1.2 * 0.9 - 1) / -0.5, 0.9)),
+    (5, "frft", 0.35 * np.exp(-2.0j)),
+    (2, "b0", (1 / 0.6, 0.0, -1.5, 0.6)),
+    (3, "lct", (1.7, -1.1, (1.7 * 0.2 - 1) / -1.1, 0.2)),
+    (11, "b0", (1 / 0.9, 0.0, 0.3, 0.9)),
+    (12, "b0", (1 / 1.9, 0.0, -0.3, 1.9)),
+]
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_ragged_smallest_sizes_both_dtypes(dtype):
+    """Ragged plans with N = 2 .. 32 (several signals per CTA), b = 0 signals
+    below and above the 2048-sample chunk of the diagonal launch, and -- in
+    complex128 -- an N = 32768 signal on the persistent two-pass kernel."""
+    specs = list(SMALL_SPECS)
+    if dtype == np.complex128:
+        specs.append((15, "lct", (0.9, -0.7, (0.9 * 0.4 - 1) / -0.7, 0.4)))
+    Ns, abcds, offs, buf, sigs = _ragged_case(specs, seed=53)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.batch(Ns, abcds, offs, dtype=code)
+    try:
+        x = torch.from_numpy(buf.astype(dtype)).cuda()
+        out = torch.zeros_like(x)
+        lct.lct_execute(p.handle, x, out, len(Ns))
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        G = out.cpu().numpy()
+    finally:
+        p.destroy()
+    tol = TOL32 if dtype == np.complex64 else TOL64
+    for N, abcd, o, f in zip(Ns, abcds, offs, sigs):
+        ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+        assert rel_l2(G[o:o + N], ref) < tol, (N, abcd)
+    mask = np.ones(len(buf), dtype=bool)
+    for N, o in zip(Ns, offs):
+        mask[o:o + N] = False
+    assert np.all(G[mask] == 0)
+
+
 def test_ragged_full_size_workload():
     """The 20000-instance ragged workload (N = 2^6..2^16, four kinds), one
     graph launch; parity on a sample of signals, Parseval on all real ones."""
