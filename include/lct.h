@@ -111,7 +111,11 @@ lct_status lct_plan_create_complex(lct_plan* out, int64_t N, const double abcd_r
 /* Batch plan: `count` independent signals, signal s of length N[s] (power of
  * two) with parameters abcd_reim[8 s .. 8 s + 7] (layout as above), stored at
  * element offset offsets[s] of the in/out buffers.  All arrays are host
- * memory, copied by the plan.  Host-only. */
+ * memory, copied by the plan.  Host-only.  A batch of mixed N, or of b = 0
+ * signals mixed with b != 0 ones, is ragged: lct_execute runs it as one CUDA
+ * graph -- one kernel per N for the b != 0 signals (the persistent two-pass
+ * kernel from N = 32768), one launch for every b = 0 signal, on concurrent
+ * branches -- captured on the first call for each (in, out) pair. */
 lct_status lct_plan_create_batch(lct_plan* out, int64_t count, const int64_t* N,
                                  const double* abcd_reim, const int64_t* offsets,
                                  lct_dtype dtype);
@@ -131,8 +135,8 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     copy while the current one is written out (complex64, N = 4096,
  *     16-byte aligned signal starts; else variant 3);
  *  5  thread-block cluster of N/8192 CTAs per signal exchanging through
- *     distributed shared memory (N = 16384 .. 65536; the only kernel for
- *     N >= 32768 in complex64 and N >= 16384 in complex128);
+ *     distributed shared memory (N = 16384 .. 65536; with variant 0 it
+ *     serves N = 16384 in complex128, where the fused kernel stops);
  *  6  paired with eight samples per thread (radix-8 passes), fewer
  *     registers and more resident warps (complex64, N = 64 .. 8192);
  *  7  two passes (four-step split N = N1 N2: column DFTs with the
