@@ -220,6 +220,24 @@ std::vector<T> build_twiddles(int log2n, int le = 4) {
     }
     return t;
 }
+
+// The cached device copy of the table `key`, built by make() on first use.
+// Caller holds g_tw_mu.
+template <class F>
+const void* cached_table(const std::tuple<int, int, int>& key, F make) {
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    const auto t = make();
+    const size_t bytes = t.size() * sizeof(t[0]);
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    g_tw[key] = d;
+    return d;
+}
 }  // namespace
 
 const void* lct_twiddle_table(int dtype, int log2n) {
@@ -227,29 +245,9 @@ const void* lct_twiddle_table(int dtype, int log2n) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> g(g_tw_mu);
-    auto key = std::make_tuple(dev, dtype, log2n);
-    auto it = g_tw.find(key);
-    if (it != g_tw.end()) return it->second;
-    void* d = nullptr;
-    size_t bytes;
-    cudaError_t e;
-    if (dtype == LCT_C64) {
-        std::vector<float> t = build_twiddles<float>(log2n);
-        bytes = t.size() * sizeof(float);
-        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
-        e = cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice);
-    } else {
-        std::vector<double> t = build_twiddles<double>(log2n);
-        bytes = t.size() * sizeof(double);
-        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
-        e = cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice);
-    }
-    if (e != cudaSuccess) {
-        cudaFree(d);
-        return nullptr;
-    }
-    g_tw[key] = d;
-    return d;
+    const auto key = std::make_tuple(dev, dtype, log2n);
+    if (dtype == LCT_C64) return cached_table(key, [&] { return build_twiddles<float>(log2n); });
+    return cached_table(key, [&] { return build_twiddles<double>(log2n); });
 }
 
 const void* lct_twiddle_table_pair(int log2n, int le) {
@@ -257,26 +255,17 @@ const void* lct_twiddle_table_pair(int log2n, int le) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> g(g_tw_mu);
-    auto key = std::make_tuple(dev, 10 + le, log2n);
-    auto it = g_tw.find(key);
-    if (it != g_tw.end()) return it->second;
-    std::vector<float> t = build_twiddles<float>(log2n, le);
-    std::vector<float> b(2 * t.size());
-    for (size_t k = 0; k < t.size() / 2; ++k) {
-        b[4 * k + 0] = t[2 * k];
-        b[4 * k + 1] = t[2 * k];
-        b[4 * k + 2] = t[2 * k + 1];
-        b[4 * k + 3] = t[2 * k + 1];
-    }
-    void* d = nullptr;
-    const size_t bytes = b.size() * sizeof(float);
-    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, b.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d);
-        return nullptr;
-    }
-    g_tw[key] = d;
-    return d;
+    return cached_table(std::make_tuple(dev, 10 + le, log2n), [&] {
+        std::vector<float> t = build_twiddles<float>(log2n, le);
+        std::vector<float> b(2 * t.size());
+        for (size_t k = 0; k < t.size() / 2; ++k) {
+            b[4 * k + 0] = t[2 * k];
+            b[4 * k + 1] = t[2 * k];
+            b[4 * k + 2] = t[2 * k + 1];
+            b[4 * k + 3] = t[2 * k + 1];
+        }
+        return b;
+    });
 }
 
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {
