@@ -26,6 +26,7 @@
 // interleaved lanes so that every warp access covers whole 32-byte sectors.
 #include "xft_engine.cuh"
 #include "xft_chirp.cuh"
+#include "xft_async.cuh"
 
 namespace {
 
@@ -199,6 +200,183 @@ k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     }
 }
 
+// Persistent form of the complex64 column kernel (radix-8 engine, G
+// interleaved columns of one field per work item, uniform parameters).  With
+// one 1024-thread CTA per SM the one-strip-per-CTA kernel cannot overlap an
+// item's loads with another's arithmetic, so here each CTA copies the strip
+// of its next item (N rows x G columns) into shared memory by cp.async while
+// it transforms the current one.  The two diagonal factors, which are the
+// same for every column, are tabulated once per CTA in shared memory.  With
+// gradients the forward output and input are read directly.  Requires count
+// and P = 2^lp to be multiples of G and 16-byte aligned strips (checked by
+// the launcher).  The descriptor is passed by value: its words stay in the
+// constant bank instead of registers.
+template <int L, int G, bool GRAD>
+struct cols_shape {
+    static constexpr int LE = 3;
+    using S = shape<L, LE>;
+    using F = gen_shape<L, G, LE>;
+    static constexpr int NT = F::THREADS, NW = NT / 32;
+    // exchange buffers: one padding slot every 2^PS samples and column
+    // buffers CO samples apart, chosen by enumerating the bank of every
+    // lane's access in every exchange so that the G interleaved columns
+    // exchange without bank conflicts (N = 1024: one 2-way store remains)
+    static constexpr int PS = L == 11 ? 2 : 3;
+    static constexpr int CO = L == 12 ? 8 : 4;
+    static constexpr int STRC = S::N + (S::N >> PS) + CO;
+    static constexpr size_t STAGE = (size_t)S::N * G;                // samples
+    static constexpr size_t WORK = (size_t)G * STRC;
+    static constexpr size_t CTAB = 2 * (size_t)S::N;
+    static constexpr size_t SMEM = (STAGE + WORK + CTAB) * sizeof(cpx<float>) +
+                                   (GRAD ? (size_t)NW * G * 3 * sizeof(double) : 0);
+    static constexpr int MIN_BLOCKS = 1024 / NT > 0 ? 1024 / NT : 1;
+};
+
+// TWT: twiddles from the engine's table tw (else computed in registers).
+template <int L, int G, bool ADJ, bool GRAD, bool TWT>
+__global__ void __launch_bounds__(gen_shape<L, G, 3>::THREADS, (cols_shape<L, G, GRAD>::MIN_BLOCKS))
+k_xft_cols(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out, const lct_desc D,
+           int64_t count, int64_t es, int lp, int64_t big, const cpx<float>* __restrict__ tw,
+           const cpx<float>* __restrict__ fwd_out, const cpx<float>* __restrict__ fwd_in,
+           double* __restrict__ partial) {
+    using C = cols_shape<L, G, GRAD>;
+    using S = typename C::S;
+    constexpr int NT = C::NT, NW = C::NW;
+    constexpr int CPR = G / 2;                                // 16-byte chunks per strip row
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* stage = reinterpret_cast<cpx<float>*>(smem_raw);     // [N][G]
+    cpx<float>* work = stage + C::STAGE;                            // [G][STRC]
+    cpx<float>* ctab = work + C::WORK;                              // [2][N]
+    double* red = reinterpret_cast<double*>(ctab + C::CTAB);        // [NW][G][3] (gradients)
+    const int tid = threadIdx.x;
+    const int sl = tid % G, i = tid / G;
+    const int64_t groups = count / G;
+    const int64_t pm = ((int64_t)1 << lp) - 1;
+
+    auto issue = [&](int64_t q) {
+        const int64_t s0 = q * G;
+        const int64_t b0 = (s0 >> lp) * big + (s0 & pm);
+        for (int j = tid; j < S::N * CPR; j += NT) {
+            const int n = j / CPR, h = j - n * CPR;
+            xasync::cp_async16(stage + n * G + 2 * h, in + b0 + (int64_t)n * es + 2 * h);
+        }
+        xasync::cp_async_commit();
+    };
+
+    int64_t q = blockIdx.x;
+    if (q < groups) issue(q);
+    {
+        // input-side and output-side factors of every sample index n
+        const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+        const float sc = (float)D.scale;
+        for (int n = tid; n < S::N; n += NT) {
+            if (ADJ) {
+                ctab[n] = cscale(conj_of(post_g<L, float>(D, n)), sc);
+                ctab[S::N + n] = conj_of(pre_g<L, float>(D, n, decay));
+            } else {
+                ctab[n] = pre_g<L, float>(D, n, decay);
+                ctab[S::N + n] = cscale(post_g<L, float>(D, n), sc);
+            }
+        }
+    }
+    for (; q < groups; q += gridDim.x) {
+        xasync::cp_async_wait_all();
+        __syncthreads();                  // strip q landed; the previous item is done with smem
+        const int64_t sig = q * G + sl;
+        const int64_t base = (sig >> lp) * big + (sig & pm);
+        float sa = 0, sr = 0, sg = 0;
+        cpx<float> v[S::E];
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int n = i + e * S::T;
+            const int64_t at = base + (int64_t)n * es;
+            const cpx<float> x = stage[n * G + sl];
+            if (GRAD) {
+                const cpx<float> Gv = fwd_out[at];
+                sr += x.x * Gv.x + x.y * Gv.y;                                // Re(conj(g) G)
+                sg += (float)m_squared(n, S::N) * (x.x * Gv.y - x.y * Gv.x);  // m^2 Im(conj(g) G)
+            }
+            v[e] = cmul(x, ctab[n]);
+        }
+        __syncthreads();                  // strip consumed: refill it with the next item
+        if (q + gridDim.x < groups) issue(q + gridDim.x);
+        dft_signal<L, ADJ ? 1 : -1, !TWT, 3, C::PS>(v, work + sl * C::STRC, i, tw);
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int n = i + e * S::T;
+            const int64_t at = base + (int64_t)n * es;
+            const cpx<float> y = cmul(v[e], ctab[S::N + n]);
+            if (GRAD) {
+                const cpx<float> fv = fwd_in[at];
+                sa += (float)m_squared(n, S::N) * (y.x * fv.y - y.y * fv.x);      // m^2 Im(conj(h) f)
+            }
+            out[at] = y;
+        }
+        if (GRAD) {
+            // per-column sums: shuffles over the lanes of a column, then the
+            // warps' partials in double, in warp order
+#pragma unroll
+            for (int o = 16; o >= G; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                sg += __shfl_xor_sync(0xffffffffu, sg, o);
+            }
+            const int lane = tid & 31, warp = tid >> 5;
+            if (lane < G) {
+                red[3 * (warp * G + lane) + 0] = sa;
+                red[3 * (warp * G + lane) + 1] = sr;
+                red[3 * (warp * G + lane) + 2] = sg;
+            }
+            __syncthreads();
+            if (i == 0) {
+                double a = 0, r = 0, g = 0;
+                for (int w = 0; w < NW; ++w) {
+                    a += red[3 * (w * G + sl) + 0];
+                    r += red[3 * (w * G + sl) + 1];
+                    g += red[3 * (w * G + sl) + 2];
+                }
+                partial[3 * sig + 0] = a;
+                partial[3 * sig + 1] = r;
+                partial[3 * sig + 2] = g;
+            }
+        }
+    }
+    xasync::cp_async_wait_all();          // no copy left in flight at exit
+}
+
+template <int L, int G, bool ADJ, bool GRAD>
+cudaError_t launch_cols(const void* in, void* out, const lct_desc& desc, int64_t count,
+                        int64_t es, int lp, int64_t big, const void* tw, const void* fwd_out,
+                        const void* fwd_in, double* partial, cudaStream_t stream) {
+    using C = cols_shape<L, G, GRAD>;
+    auto kern = tw ? k_xft_cols<L, G, ADJ, GRAD, true> : k_xft_cols<L, G, ADJ, GRAD, false>;
+    static int per_sm[2][64] = {}, sms[64] = {};
+    const int t = tw ? 1 : 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!per_sm[t][dev]) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::SMEM)) != cudaSuccess)
+            return e;
+        int nb = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::NT, C::SMEM)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        per_sm[t][dev] = nb > 0 ? nb : 1;
+    }
+    const int64_t groups = count / G;
+    const int64_t slots = (int64_t)per_sm[t][dev] * sms[dev];
+    const int64_t grid = groups < slots ? groups : slots;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<(unsigned)grid, C::NT, C::SMEM, stream>>>(
+        (const cpx<float>*)in, (cpx<float>*)out, desc, count, es, lp, big, (const cpx<float>*)tw,
+        (const cpx<float>*)fwd_out, (const cpx<float>*)fwd_in, partial);
+    return cudaGetLastError();
+}
+
 template <int L, class R, int G, bool ADJ, bool GRAD, int LE = 4>
 cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc_step,
                        int64_t count, const void* tw, int64_t es, int64_t P, int64_t big,
@@ -227,8 +405,30 @@ cudaError_t launch_gen(const void* in, void* out, const lct_desc* desc, int desc
 // N = 4096, so that a CTA stays within 1024 threads).
 template <bool ADJ, bool GRAD>
 cudaError_t gen_cols8(int log2n, const void* in, void* out, const lct_desc* desc, int desc_step,
-                      int64_t count, int64_t es, int64_t P, int64_t big, const void* fo,
-                      const void* fi, double* partial, cudaStream_t stream) {
+                      int64_t count, const void* tw8, int64_t es, int64_t P, int64_t big,
+                      const void* fo, const void* fi, double* partial, const lct_desc* host_desc,
+                      cudaStream_t stream) {
+    // the persistent staged kernel: uniform parameters known on the host,
+    // whole groups of columns, P a power of two, 16-byte aligned strips
+    const int G = log2n == 12 ? 2 : 4;
+    int lp = 0;
+    while (lp < 62 && ((int64_t)1 << lp) < P) ++lp;
+    const bool staged = host_desc && desc_step == 0 && log2n >= 9 && ((int64_t)1 << lp) == P &&
+                        count % G == 0 && P % G == 0 && es % 2 == 0 && big % 2 == 0 &&
+                        ((uintptr_t)in) % 16 == 0;
+    if (staged) {
+        const lct_desc& hd = *host_desc;
+        // twiddles: computed in registers without gradients (measured faster),
+        // read from the radix-8 table with them (fewer registers)
+        const void* tw8k = GRAD ? tw8 : nullptr;
+        switch (log2n) {
+            case 9: return launch_cols<9, 4, ADJ, GRAD>(in, out, hd, count, es, lp, big, tw8k, fo, fi, partial, stream);
+            case 10: return launch_cols<10, 4, ADJ, GRAD>(in, out, hd, count, es, lp, big, tw8k, fo, fi, partial, stream);
+            case 11: return launch_cols<11, 4, ADJ, GRAD>(in, out, hd, count, es, lp, big, tw8k, fo, fi, partial, stream);
+            case 12: return launch_cols<12, 2, ADJ, GRAD>(in, out, hd, count, es, lp, big, tw8k, fo, fi, partial, stream);
+            default: break;
+        }
+    }
     switch (log2n) {
 #define LCT_CASE8(L, G)                                                                          \
     case L:                                                                                      \
@@ -363,17 +563,17 @@ cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad
                            void* out, const lct_desc* desc, int desc_step, int64_t count,
                            const void* tw, int64_t es, int64_t P, int64_t big,
                            const void* fwd_out, const void* fwd_in, double* partial,
-                           cudaStream_t stream) {
+                           const lct_desc* host_desc, cudaStream_t stream) {
     if (dtype == 0) {
         if (cols) {
             if (!adjoint)
-                return gen_cols8<false, false>(log2n, in, out, desc, desc_step, count, es, P, big,
-                                               fwd_out, fwd_in, partial, stream);
+                return gen_cols8<false, false>(log2n, in, out, desc, desc_step, count, tw, es, P,
+                                               big, fwd_out, fwd_in, partial, host_desc, stream);
             if (!grad)
-                return gen_cols8<true, false>(log2n, in, out, desc, desc_step, count, es, P, big,
-                                              fwd_out, fwd_in, partial, stream);
-            return gen_cols8<true, true>(log2n, in, out, desc, desc_step, count, es, P, big,
-                                         fwd_out, fwd_in, partial, stream);
+                return gen_cols8<true, false>(log2n, in, out, desc, desc_step, count, tw, es, P,
+                                              big, fwd_out, fwd_in, partial, host_desc, stream);
+            return gen_cols8<true, true>(log2n, in, out, desc, desc_step, count, tw, es, P, big,
+                                         fwd_out, fwd_in, partial, host_desc, stream);
         }
         return gen_mode<float, 1>(log2n, adjoint, grad, in, out, desc, desc_step, count, tw, es, P,
                                   big, fwd_out, fwd_in, partial, stream);

@@ -250,6 +250,14 @@ const void* lct_twiddle_table(int dtype, int log2n) {
     return cached_table(key, [&] { return build_twiddles<double>(log2n); });
 }
 
+const void* lct_twiddle_table_r8(int log2n) {
+    if (log2n < 4) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    return cached_table(std::make_tuple(dev, 30, log2n), [&] { return build_twiddles<float>(log2n, 3); });
+}
+
 const void* lct_twiddle_table_pair(int log2n, int le) {
     if (log2n <= le) return nullptr;
     int dev = -1;
@@ -933,7 +941,9 @@ lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G,
                         cudaStream_t stream) {
     const int log2n = p->desc[0].log2n;
     if (!lct_gen_supported(p->dtype, log2n, cols)) return LCT_ERR_UNSUPPORTED;
-    const void* tw = lct_twiddle_table(p->dtype, log2n);
+    // complex64 columns run the radix-8 engine
+    const bool r8 = cols && p->dtype == LCT_C64;
+    const void* tw = r8 ? lct_twiddle_table_r8(log2n) : lct_twiddle_table(p->dtype, log2n);
     if (log2n >= 5 && !tw) return LCT_ERR_OOM;
     const int do_grad = grad != nullptr;
     if (do_grad) {
@@ -943,7 +953,8 @@ lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G,
     const int desc_step = p->is_batch ? 1 : 0;
     lct_status st = from_cuda(lct_launch_gen(p->dtype, log2n, cols, 1, do_grad, g, h, p->d_desc,
                                              desc_step, batch, tw, es, P, big, G, f,
-                                             do_grad ? p->d_partial : nullptr, stream));
+                                             do_grad ? p->d_partial : nullptr,
+                                             desc_step ? nullptr : p->desc.data(), stream));
     if (st != LCT_OK || !do_grad) return st;
     return from_cuda(lct_launch_grad_finalize(p->d_partial, p->d_coef, desc_step, batch,
                                               p->is_batch ? 0 : 1, grad,
@@ -1443,13 +1454,13 @@ lct_status lct2d_execute(lct2d_plan plan, const void* in, void* mid, void* out, 
     st = ensure_device(py);
     if (st != LCT_OK) return st;
     const int ly = py->desc[0].log2n;
-    const void* tw = lct_twiddle_table(py->dtype, ly);
+    const void* tw = py->dtype == LCT_C64 ? lct_twiddle_table_r8(ly) : lct_twiddle_table(py->dtype, ly);
     if (ly >= 5 && !tw) return LCT_ERR_OOM;
     // columns: batch * nx signals of length ny, element stride nx
     return from_cuda(lct_launch_gen(py->dtype, ly, 1, 0, 0, mid, out, py->d_desc, 0,
                                     batch * plan->nx, tw, plan->nx, plan->nx,
                                     plan->nx * plan->ny, nullptr, nullptr, nullptr,
-                                    (cudaStream_t)stream_));
+                                    py->desc.data(), (cudaStream_t)stream_));
 }
 
 lct_status lct2d_backward(lct2d_plan plan, const void* grad_out, const void* in, const void* mid,

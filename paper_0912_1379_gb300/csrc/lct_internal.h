@@ -54,6 +54,9 @@ int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D);
 // entry e^{-2 pi i j k / (16 Ns_p)}, Ns_p = R0 16^(p-1), R0 the first radix.
 // Returns nullptr on failure (and for N < 32, which needs no table).
 const void* lct_twiddle_table(int dtype, int log2n);
+// Complex64 table of the radix-8 engine (8 samples per thread), same
+// layout with radix 8: the column kernels' twiddles.
+const void* lct_twiddle_table_r8(int log2n);
 // Broadcast form of the complex64 table for the paired kernels (radix
 // 2^le passes, le = 4 or 3): every entry (wx, wy) stored as
 // {(wx, wx), (wy, wy)} (16 bytes).
@@ -165,12 +168,18 @@ cudaError_t lct_launch_diag_chunks(int dtype, const void* in, void* out, const l
 // (cols = 0) or interleaved columns (cols = 1), optional gradient sums
 // (SA, SR, SG) per signal into partial[3 s ..].  Signal s starts at D.offset
 // (desc_step = 1) or (s / P) * big + (s % P); element stride es.
+// host_desc (may be null): a host copy of desc[0]; with it, complex64
+// columns of uniform parameters run the persistent kernel that stages the
+// next strip in shared memory (P a power of two, whole groups of columns,
+// 16-byte aligned strips), else the one-strip-per-CTA kernel.  tw: the
+// table of lct_twiddle_table(dtype, log2n), except for complex64 columns:
+// lct_twiddle_table_r8(log2n) (or null: twiddles computed in registers).
 bool lct_gen_supported(int dtype, int log2n, int cols);
 cudaError_t lct_launch_gen(int dtype, int log2n, int cols, int adjoint, int grad, const void* in,
                            void* out, const lct_desc* desc, int desc_step, int64_t count,
                            const void* tw, int64_t es, int64_t P, int64_t big,
                            const void* fwd_out, const void* fwd_in, double* partial,
-                           cudaStream_t stream);
+                           const lct_desc* host_desc, cudaStream_t stream);
 // grad[3 s + {0,1,2}] = (dl/da, dl/db, dl/dd) from the sums; coef: 5 doubles
 // per signal (coef_step 1) or shared (coef_step 0); shared != 0 sums over
 // the signals into grad[0..2].

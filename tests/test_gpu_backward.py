@@ -176,6 +176,46 @@ def test_2d_forward_backward_vs_oracle(ny, nx, dt):
     assert grad_rel(gp[3:], gy) < gtol
 
 
+@pytest.mark.parametrize("ny,nx,B", [(512, 8, 1), (1024, 4, 3), (2048, 16, 1), (4096, 8, 1),
+                                      (2048, 2, 1)])
+def test_2d_column_kernels(ny, nx, B):
+    """The column passes at N = 512 .. 4096: whole groups of columns run the
+    persistent kernel that stages the next strip in shared memory (and
+    tabulates the diagonal factors), nx = 2 with B = 1 the per-strip kernel;
+    forward, adjoint without and with the gradient sums, against the oracle."""
+    ax = (0.6, 1.2, (0.6 * -0.5 - 1) / 1.2, -0.5)
+    ay = (-0.9, 0.7, (-0.9 * 1.1 - 1) / 0.7, 1.1)
+    f = field(ny, nx, B, 11, np.complex64)
+    rng = np.random.default_rng(12)
+    g = (rng.standard_normal((B, ny, nx)) + 1j * rng.standard_normal((B, ny, nx))).astype(np.complex64)
+    plan = lct.lct2d_plan_create(ny, nx, ay, ax, lct.LCT_C64)
+    try:
+        xf, xg = cu(f), cu(g)
+        mid, out = torch.empty_like(xf), torch.empty_like(xf)
+        lct.lct2d_execute(plan, xf, mid, out, B)
+        gmid, gin = torch.empty_like(xf), torch.empty_like(xf)
+        lct.lct2d_backward(plan, xg, xf, mid, out, gmid, gin, None, B)
+        torch.cuda.synchronize()
+        gin0 = gin.cpu().numpy()
+        gp = torch.zeros(6, dtype=torch.float64, device="cuda")
+        lct.lct2d_backward(plan, xg, xf, mid, out, gmid, gin, gp, B)
+        torch.cuda.synchronize()
+        out, gin, gp = out.cpu().numpy(), gin.cpu().numpy(), gp.cpu().numpy()
+    finally:
+        lct.lct2d_plan_destroy(plan)
+    f64, g64 = f.astype(np.complex128), g.astype(np.complex128)
+    ref_mid, ref_out = oracle_2d(f64, ax, ay)
+    assert rel_l2(out.reshape(B, -1), ref_out.reshape(B, -1)).max() < 1e-5
+    gcol = O.lct_adjoint(np.swapaxes(g64, 1, 2).reshape(-1, ny), ay).reshape(B, nx, ny)
+    gmid_ref = np.swapaxes(gcol, 1, 2)
+    gin_ref = O.lct_adjoint(gmid_ref.reshape(-1, nx), ax).reshape(B, ny, nx)
+    assert rel_l2(gin0.reshape(B, -1), gin_ref.reshape(B, -1)).max() < 1e-5
+    assert rel_l2(gin.reshape(B, -1), gin_ref.reshape(B, -1)).max() < 1e-5
+    gy = O.lct_grad_params(np.swapaxes(ref_mid, 1, 2).reshape(-1, ny),
+                           np.swapaxes(g64, 1, 2).reshape(-1, ny), np.tile(ay, (B * nx, 1))).sum(axis=0)
+    assert grad_rel(gp[3:], gy) < 1e-4
+
+
 def test_2d_full_size_fields():
     """8 fields of 2048 x 2048 (complex64): Gaussian beam times a smooth random
     phase screen; Parseval and the adjoint identity at full size, and the
