@@ -277,8 +277,9 @@ lct_status lct_execute_noalloc(int64_t N, double a, double b, double c, double d
 const char* lct_status_string(lct_status status);
 
 /* Debug mode (also enabled by the environment variable LCT_DEBUG=1, read
- * once): every lct_execute then synchronises its stream, scans its output
- * signals for NaN or infinite samples and returns LCT_ERR_DEVICE if one is
+ * once): every lct_execute (its output) and lct_backward (its grad_in) then
+ * synchronises its stream, scans those signals for NaN or infinite samples
+ * and returns LCT_ERR_DEVICE if one is
  * found or a kernel recorded a per-item error (LCT_ERR_TIMEOUT for a timed-
  * out wait), clearing the device status word.  on = 0 turns it off. */
 lct_status lct_set_debug(int on);

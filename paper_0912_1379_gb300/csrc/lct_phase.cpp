@@ -1,0 +1,270 @@
+// Exact phase constants, per-signal descriptors and the Stockham twiddle
+// tables (host side of the chirp phases of Sec. 3, Algorithm, steps 1-2).
+//
+// Phase constants.  The chirp coefficients
+//   Re(beta_in)/(2 pi)  = Re(a/b) pi / (32 N)
+//   Re(beta_out)/(2 pi) = Re(b d) / (2 pi N)
+// are evaluated in double-double arithmetic (about 106 significant bits)
+// from the exact FP64 parameters and reduced modulo one turn into 128-bit
+// fixed-point fractions.  The output constant e^{-i pi (N-1)^2/(2N)} is an
+// exact dyadic turn fraction; the argument of dx/sqrt(2 pi i b) is added to
+// it in double precision.
+#include "lct_plan.h"
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+namespace lcth {
+
+// ---------------------------------------------------------------------------
+// double-double arithmetic (Dekker / Knuth error-free transformations)
+// ---------------------------------------------------------------------------
+struct dd { double hi, lo; };
+
+dd two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+dd quick_two_sum(double a, double b) {
+    double s = a + b;
+    return {s, b - (s - a)};
+}
+dd two_prod(double a, double b) {
+    double p = a * b;
+    return {p, std::fma(a, b, -p)};
+}
+dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi);
+    dd t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+dd dd_mul(dd a, dd b) {
+    dd p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return quick_two_sum(p.hi, p.lo);
+}
+dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(b, {q1, 0.0}));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(b, {q2, 0.0}));
+    double q3 = r.hi / b.hi;
+    return dd_add(quick_two_sum(q1, q2), {q3, 0.0});
+}
+dd dd_ldexp(dd a, int e) { return {std::ldexp(a.hi, e), std::ldexp(a.lo, e)}; }
+
+// pi to about 107 bits
+const dd DD_PI = {3.141592653589793116e+00, 1.224646799147353207e-16};
+
+typedef unsigned __int128 u128;
+
+// round(v * 2^128) mod 2^128 for |v| < 1.
+u128 frac_to_q128(double v) {
+    if (v == 0.0) return 0;
+    int e;
+    double m = std::frexp(std::fabs(v), &e);          // |v| = m 2^e, m in [1/2, 1)
+    uint64_t M = (uint64_t)std::ldexp(m, 53);         // exact 53-bit integer
+    int sh = e - 53 + 128;                            // |v| 2^128 = M 2^sh, sh <= 75
+    u128 r;
+    if (sh >= 0) r = (u128)M << sh;
+    else if (sh > -64) r = (u128)((M + ((uint64_t)1 << (-sh - 1))) >> (-sh));
+    else r = 0;
+    return v < 0 ? (u128)0 - r : r;
+}
+
+// Fractional part of a double-double as a 128-bit turn fraction.
+void dd_to_turns128(dd t, uint64_t* hi, uint64_t* lo) {
+    // x - trunc(x) is exact for every double (x - floor(x) is not for small
+    // negative x); the signed fractions wrap modulo one turn below.
+    double fh = t.hi - std::trunc(t.hi);
+    double fl = t.lo - std::trunc(t.lo);
+    u128 q = frac_to_q128(fh) + frac_to_q128(fl);
+    *hi = (uint64_t)(q >> 64);
+    *lo = (uint64_t)q;
+}
+
+// Fractional part of a double (|v| moderate) as a 64-bit turn fraction.
+uint64_t double_to_turns64(double v) {
+    uint64_t hi, lo;
+    dd_to_turns128({v, 0.0}, &hi, &lo);
+    return hi + (lo >> 63);
+}
+
+typedef std::complex<double> cplx;
+
+int ilog2_exact(int64_t N) {
+    if (N < 2 || N > 65536) return -1;
+    if ((N & (N - 1)) != 0) return -1;
+    int p = 0;
+    while ((int64_t(1) << p) < N) ++p;
+    return p;
+}
+
+// Re(x/y) of complex FP64 numbers, in double-double.
+dd dd_re_div(cplx x, cplx y) {
+    dd num = dd_add(two_prod(x.real(), y.real()), two_prod(x.imag(), y.imag()));
+    dd den = dd_add(two_prod(y.real(), y.real()), two_prod(y.imag(), y.imag()));
+    return dd_div(num, den);
+}
+// Re(x*y) in double-double.
+dd dd_re_mul(cplx x, cplx y) {
+    return dd_sub(two_prod(x.real(), y.real()), two_prod(x.imag(), y.imag()));
+}
+
+bool symplectic(cplx a, cplx b, cplx c, cplx d) {
+    cplx ad = a * d, bc = b * c;
+    double tol = 1e-9 * std::fmax(1.0, std::fmax(std::abs(ad), std::abs(bc)));
+    return std::abs(ad - bc - 1.0) <= tol;
+}
+
+// Build the descriptor of one signal.  Returns LCT_OK or a validation error.
+lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
+    int log2n = ilog2_exact(N);
+    if (log2n < 0) return LCT_ERR_N;
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(p[i])) return LCT_ERR_ARG;
+    cplx a(p[0], p[1]), b(p[2], p[3]), c(p[4], p[5]), d(p[6], p[7]);
+    if (!symplectic(a, b, c, d)) return LCT_ERR_NOT_SYMPLECTIC;
+    std::memset(D, 0, sizeof(*D));
+    D->offset = offset;
+    D->log2n = log2n;
+    uint64_t hi, lo;
+    if (b == cplx(0.0, 0.0)) {
+        // b = 0: G_j = sqrt(d) e^{i c x_j^2 / (2d)} f_j on y_j = x_j / d;
+        // c x^2/(2d) = Re(c/d) pi^2 m^2/(16N) -> turns Re(c/d) pi / (32N).
+        D->kind = LCT_KIND_DIAG;
+        dd t = dd_ldexp(dd_mul(dd_re_div(c, d), DD_PI), -(5 + log2n));
+        dd_to_turns128(t, &hi, &lo);
+        D->out_hi = hi;
+        D->out_lo = lo;
+        cplx sd = std::sqrt(d);                       // principal root
+        D->scale = std::abs(sd);
+        D->out_c = double_to_turns64(std::arg(sd) / (2.0 * M_PI));
+        return LCT_OK;
+    }
+    D->kind = LCT_KIND_XFT;
+    // pre-chirp a x_k^2/(2b) = (a/b) pi^2 m^2 / (16 N): turns (a/b) pi / (32 N)
+    dd tin = dd_ldexp(dd_mul(dd_re_div(a, b), DD_PI), -(5 + log2n));
+    dd_to_turns128(tin, &hi, &lo);
+    D->in_hi = hi;
+    D->in_lo = lo;
+    cplx ab = a / b;
+    double decay = ab.imag() * M_PI * M_PI / (16.0 * (double)N);
+    D->decay = decay;
+    if (decay != 0.0) D->flags |= LCT_FLAG_DECAY;
+    // post-chirp d y_j^2/(2b) = b d m^2 / N: turns Re(b d) / (2 pi N)
+    dd tout = dd_ldexp(dd_div(dd_re_mul(b, d), DD_PI), -(1 + log2n));
+    dd_to_turns128(tout, &hi, &lo);
+    D->out_hi = hi;
+    D->out_lo = lo;
+    // constant: -(N-1)^2/(4N) turns (exact) + arg(dx / sqrt(2 pi i b)) / (2 pi)
+    uint64_t r = (uint64_t)(((N - 1) * (N - 1)) % (4 * N));
+    uint64_t centre = (uint64_t)0 - (r << (62 - log2n));       // -r / (4N) as Q0.64
+    double dx = M_PI / std::sqrt(2.0 * (double)N);
+    cplx pre = dx / std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
+    D->scale = std::abs(pre);
+    D->out_c = centre + double_to_turns64(std::arg(pre) / (2.0 * M_PI));
+    return LCT_OK;
+}
+
+}  // namespace lcth
+
+using namespace lcth;
+
+// ---------------------------------------------------------------------------
+// twiddle tables of the Stockham engine (xft_engine.cuh)
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tw_mu;
+std::map<std::tuple<int, int, int>, void*> g_tw;   // (device, dtype, log2n) -> table
+
+// Table of the Stockham engine with radix E = 2^le passes (see xft_engine.cuh).
+template <class T>
+std::vector<T> build_twiddles(int log2n, int le = 4) {
+    const int E = 1 << le;
+    const int P = log2n >= le ? (log2n + le - 1) / le : 1;
+    const int R0 = 1 << (log2n - le * (P - 1));
+    std::vector<T> t;
+    for (int p = 1; p < P; ++p) {
+        const int64_t ns = (int64_t)R0 << (le * (p - 1));
+        const int64_t M = E * ns;
+        for (int j = 1; j < E; ++j)
+            for (int64_t k = 0; k < ns; ++k) {
+                const double ang = 2.0 * M_PI * (double)((j * k) % M) / (double)M;
+                t.push_back((T)std::cos(ang));
+                t.push_back((T)-std::sin(ang));
+            }
+    }
+    return t;
+}
+
+// The cached device copy of the table `key`, built by make() on first use.
+// Caller holds g_tw_mu.
+template <class F>
+const void* cached_table(const std::tuple<int, int, int>& key, F make) {
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    const auto t = make();
+    const size_t bytes = t.size() * sizeof(t[0]);
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, t.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    g_tw[key] = d;
+    return d;
+}
+}  // namespace
+
+const void* lct_twiddle_table(int dtype, int log2n) {
+    if (log2n < 5) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    const auto key = std::make_tuple(dev, dtype, log2n);
+    if (dtype == LCT_C64) return cached_table(key, [&] { return build_twiddles<float>(log2n); });
+    return cached_table(key, [&] { return build_twiddles<double>(log2n); });
+}
+
+const void* lct_twiddle_table_r8(int log2n) {
+    if (log2n < 4) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    return cached_table(std::make_tuple(dev, 30, log2n), [&] { return build_twiddles<float>(log2n, 3); });
+}
+
+const void* lct_twiddle_table_pair(int log2n, int le) {
+    if (log2n <= le) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    return cached_table(std::make_tuple(dev, 10 + le, log2n), [&] {
+        std::vector<float> t = build_twiddles<float>(log2n, le);
+        std::vector<float> b(2 * t.size());
+        for (size_t k = 0; k < t.size() / 2; ++k) {
+            b[4 * k + 0] = t[2 * k];
+            b[4 * k + 1] = t[2 * k];
+            b[4 * k + 2] = t[2 * k + 1];
+            b[4 * k + 3] = t[2 * k + 1];
+        }
+        return b;
+    });
+}
+
+int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {
+    return (int)make_desc(N, p, offset, D);
+}

@@ -1,0 +1,137 @@
+// Host-side internals of the library, shared by lct_phase.cpp (exact phase
+// constants, descriptors, twiddle tables), lct_plan.cpp (plans, device
+// state, tune cache, sharding), lct_exec.cpp (forward execution) and
+// lct_grad.cpp (backward and the separable 2-D transform): the plan object
+// and the helpers the entry points share.  Not installed; include/lct.h is
+// the public interface.
+#pragma once
+#include "lct_internal.h"
+#include "../../include/lct.h"
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <complex>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct lct_plan_s {
+    lct_dtype dtype = LCT_C64;
+    lct_precision prec = LCT_PREC_NATIVE;
+    bool is_batch = false;
+    int64_t count = 1;
+    int64_t N0 = 0;                 // common N (uniform plans); 0 when ragged
+    std::vector<int64_t> N;
+    std::vector<double> abcd;       // count x 8
+    std::vector<lct_desc> desc;     // count descriptors
+    // device state
+    std::mutex mu;
+    int device = -1;
+    lct_desc* d_desc = nullptr;
+    int32_t* d_status = nullptr;
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+    void* d_tp = nullptr;            // two-pass chunk workspace(s)
+    size_t tp_bytes = 0;
+    cufftHandle fft = 0;
+    bool fft_valid = false;
+    int64_t fft_n = 0, fft_batch = 0;
+    int variant = -1;               // -1: not chosen (cache or default 0)
+    // ragged execution (mixed N or kinds): groups of equal (N, kind), largest
+    // N first, each an index list into desc; run as one CUDA graph
+    // kind LCT_KIND_DIAG: one group for every diagonal signal (log2n = -1),
+    // its idx list ordered by N, run through the chunk list chunks[chunk_off ..]
+    struct group {
+        int log2n, kind;
+        int64_t count, idx_off;
+        int64_t tp_off = -1;
+        int64_t chunk_off = 0, nchunks = 0;
+    };
+    bool ragged = false;
+    std::vector<group> groups;
+    std::vector<int32_t> idx;       // concatenated index lists
+    int32_t* d_idx = nullptr;
+    std::vector<int32_t> chunks;    // diagonal-group chunks, 4 int32 each
+    int32_t* d_chunks = nullptr;
+    static constexpr int kBranches = 4;
+    cudaStream_t cap = nullptr;
+    cudaStream_t side[kBranches] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBranches] = {};
+    cudaGraphExec_t gexec = nullptr;
+    // host-buffer execution: copy-in, compute and copy-out streams, two
+    // staging buffer pairs of `hx_chunk` signals, and their events
+    cudaStream_t hx_stream[3] = {};
+    cudaEvent_t hx_start = nullptr;
+    cudaEvent_t hx_in[2] = {}, hx_comp[2] = {}, hx_out[2] = {};
+    void* hx_buf = nullptr;
+    size_t hx_bytes = 0;
+    const void* g_in = nullptr;
+    void* g_out = nullptr;
+    // backward: per-signal gradient coefficients and reduction workspace
+    double* d_coef = nullptr;
+    double* d_partial = nullptr;
+    int64_t partial_count = 0;
+    // offset properties, fixed at creation: every offset even (16-byte signal
+    // starts when `in` is 16-byte aligned) and offset[s] == s N0
+    bool even_offsets = true;
+    bool contiguous = true;
+};
+
+namespace lcth {
+
+typedef std::complex<double> cplx;
+
+// ---- lct_phase.cpp --------------------------------------------------------
+// log2 N for N a power of two in [2, 65536], else -1.
+int ilog2_exact(int64_t N);
+// round(v 2^64) mod 2^64 for a turn fraction v (|v| < 1).
+uint64_t double_to_turns64(double v);
+// Validates p = {a, b, c, d} (re, im pairs; ad - bc = 1) and fills the
+// descriptor of one N-point signal at element `offset`.
+lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D);
+
+// ---- lct_plan.cpp ---------------------------------------------------------
+int tune_lookup(int dtype, int log2n);               // -1: no cached choice
+void tune_store(int dtype, int log2n, int variant);
+void release_device(lct_plan p);
+lct_status ensure_device(lct_plan p);                // descriptors on the current device
+bool debug_on();
+lct_status check_ptr(const void* ptr, lct_dtype dt);
+lct_status from_cuda(cudaError_t e);
+lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t* N,
+                    const double* abcd, const int64_t* offsets, bool is_batch);
+
+// ---- lct_exec.cpp ---------------------------------------------------------
+int default_variant(lct_dtype dtype, int log2n);
+int effective_variant(lct_plan p);
+bool tma_aligned(lct_plan p, const void* in);
+bool pair_tma_ok(lct_plan p, const void* in);
+bool tma_ok(lct_plan p, const void* in);
+lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, void* out,
+                          int64_t batch, cudaStream_t stream);
+lct_status debug_check(lct_plan plan, const void* out, int64_t count, cudaStream_t stream);
+
+// ---- lct_grad.cpp ---------------------------------------------------------
+bool real_params(const lct_plan p);
+lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G, void* h,
+                        double* grad, int64_t batch, int cols, int64_t es, int64_t P, int64_t big,
+                        cudaStream_t stream);
+
+inline size_t sample_bytes(lct_dtype dtype) { return dtype == LCT_C64 ? 8 : 16; }
+
+// NVTX range over an entry point (visible in Nsight timelines; costs a
+// call into the NVTX stub when no tool is attached).
+struct trace_range {
+    explicit trace_range(const char* name) { nvtxRangePushA(name); }
+    ~trace_range() { nvtxRangePop(); }
+    trace_range(const trace_range&) = delete;
+    trace_range& operator=(const trace_range&) = delete;
+};
+
+}  // namespace lcth

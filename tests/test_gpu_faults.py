@@ -48,8 +48,8 @@ def test_bounded_wait_times_out_and_context_survives(which):
 @pytest.mark.parametrize("batch_plan", [False, True])
 def test_debug_mode_flags_nonfinite_output(batch_plan):
     """LCT_DEBUG / lct_set_debug: a NaN in the input reaches the output and
-    lct_execute reports LCT_ERR_DEVICE (8); finite data passes; off again,
-    nothing is checked."""
+    lct_execute reports LCT_ERR_DEVICE (8), as does lct_backward for a NaN
+    in its cotangent; finite data passes; off again, nothing is checked."""
     N, count = 256, 8
     x = O.nodes(N)
     params, f = W.uniform_batch(x, count, seed=4, dtype=np.complex64)
@@ -69,6 +69,13 @@ def test_debug_mode_flags_nonfinite_output(batch_plan):
             lct.lct_execute(p.handle, xbad, out, count)
         assert e.value.status == 8
         assert lct.lct_device_status(p.handle) == 0             # the word was cleared
+        # lct_backward scans its grad_in the same way
+        gin = torch.empty_like(xin)
+        lct.lct_backward(p.handle, xin, xin, out, gin, None, count)    # finite: no error
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_backward(p.handle, xbad, xin, out, gin, None, count)
+        assert e.value.status == 8
+        assert lct.lct_device_status(p.handle) == 0
         lct.lct_set_debug(False)
         lct.lct_execute(p.handle, xbad, out, count)             # not checked when off
         torch.cuda.synchronize()
