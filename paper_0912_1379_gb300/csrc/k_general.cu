@@ -299,7 +299,18 @@ k_xft_cols(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out, cons
             v[e] = cmul(x, ctab[n]);
         }
         __syncthreads();                  // strip consumed: refill it with the next item
-        if (q + gridDim.x < groups) issue(q + gridDim.x);
+        if (q + gridDim.x < groups) {
+            issue(q + gridDim.x);
+            if (GRAD) {
+                // the next item's rows of the forward output and input into L2
+                const int64_t s1 = (q + gridDim.x) * G;
+                const int64_t b1 = (s1 >> lp) * big + (s1 & pm);
+                for (int n = tid; n < S::N; n += NT) {
+                    xasync::prefetch_l2(fwd_out + b1 + (int64_t)n * es);
+                    xasync::prefetch_l2(fwd_in + b1 + (int64_t)n * es);
+                }
+            }
+        }
         dft_signal<L, ADJ ? 1 : -1, !TWT, 3, C::PS>(v, work + sl * C::STRC, i, tw);
 #pragma unroll
         for (int e = 0; e < S::E; ++e) {
