@@ -339,16 +339,30 @@ k_xft_cols(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out, cons
                 red[3 * (warp * G + lane) + 2] = sg;
             }
             __syncthreads();
-            if (i == 0) {
-                double a = 0, r = 0, g = 0;
-                for (int w = 0; w < NW; ++w) {
-                    a += red[3 * (w * G + sl) + 0];
-                    r += red[3 * (w * G + sl) + 1];
-                    g += red[3 * (w * G + sl) + 2];
+            if (warp == 0) {
+                // warp 0 adds the warps' partials in double: lane c + G r
+                // takes column c's partials of warps r, r + 32/G, ..., then
+                // a shuffle tree over r (a fixed order: deterministic)
+                constexpr int SL = 32 / G;
+                const int c = lane % G, r = lane / G;
+                double a = 0, rs = 0, g = 0;
+                for (int w = r; w < NW; w += SL) {
+                    a += red[3 * (w * G + c) + 0];
+                    rs += red[3 * (w * G + c) + 1];
+                    g += red[3 * (w * G + c) + 2];
                 }
-                partial[3 * sig + 0] = a;
-                partial[3 * sig + 1] = r;
-                partial[3 * sig + 2] = g;
+#pragma unroll
+                for (int o = G; o < 32; o <<= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if (r == 0) {
+                    const int64_t sc = q * G + c;
+                    partial[3 * sc + 0] = a;
+                    partial[3 * sc + 1] = rs;
+                    partial[3 * sc + 2] = g;
+                }
             }
         }
     }
