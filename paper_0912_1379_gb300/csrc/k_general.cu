@@ -176,25 +176,53 @@ k_xft_gen(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
                 red[3 * warp + 2] = sg;
             }
             __syncthreads();
-            if (i == 0 && active) {
-                double a = 0, r = 0, g = 0;
-                if (G > 1) {
-                    for (int w = 0; w < NW; ++w) {
-                        a += red[3 * (w * G + sl) + 0];
-                        r += red[3 * (w * G + sl) + 1];
-                        g += red[3 * (w * G + sl) + 2];
+            // the warps' partials added in double by a shuffle tree (a fixed
+            // order: deterministic).  Columns: warp 0, lane c + G r takes
+            // column c's partials of warps r, r + 32/G, ...  Rows: the
+            // signal's first warp, lane w its warp w (T/32 <= 32 warps).
+            if (G > 1) {
+                if (warp == 0) {
+                    constexpr int SL = 32 / G;
+                    const int c = lane % G, r = lane / G;
+                    double a = 0, rs = 0, g = 0;
+                    for (int w = r; w < NW; w += SL) {
+                        a += red[3 * (w * G + c) + 0];
+                        rs += red[3 * (w * G + c) + 1];
+                        g += red[3 * (w * G + c) + 2];
                     }
-                } else {
-                    const int w0 = (sl * S::T) >> 5, nw = S::T >> 5;
-                    for (int w = w0; w < w0 + nw; ++w) {
-                        a += red[3 * w + 0];
-                        r += red[3 * w + 1];
-                        g += red[3 * w + 2];
+#pragma unroll
+                    for (int o = G; o < 32; o <<= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, o);
+                        rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                        g += __shfl_xor_sync(0xffffffffu, g, o);
+                    }
+                    const int64_t sc = (int64_t)blockIdx.x * F::SPC + c;
+                    if (r == 0 && sc < count) {
+                        partial[3 * sc + 0] = a;
+                        partial[3 * sc + 1] = rs;
+                        partial[3 * sc + 2] = g;
                     }
                 }
-                partial[3 * sig + 0] = a;
-                partial[3 * sig + 1] = r;
-                partial[3 * sig + 2] = g;
+            } else if (i < 32) {
+                constexpr int NWS = S::T / 32;             // warps per signal
+                const int w0 = (sl * S::T) >> 5;
+                double a = 0, rs = 0, g = 0;
+                if (lane < NWS) {
+                    a = red[3 * (w0 + lane) + 0];
+                    rs = red[3 * (w0 + lane) + 1];
+                    g = red[3 * (w0 + lane) + 2];
+                }
+#pragma unroll
+                for (int o = 1; o < NWS; o <<= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if (i == 0 && active) {
+                    partial[3 * sig + 0] = a;
+                    partial[3 * sig + 1] = rs;
+                    partial[3 * sig + 2] = g;
+                }
             }
         }
     }
