@@ -14,6 +14,7 @@
 
 namespace lcth {
 
+namespace {
 // Plain FP64 path: chirp kernel -> cuFFT Z2Z (forward) -> chirp+scale kernel.
 lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int desc_step,
                      cudaStream_t stream) {
@@ -47,6 +48,7 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
     return from_cuda(lct_launch_plain_post(p->dtype, log2n, p->d_work, out, p->d_desc, desc_step,
                                            count, stream));
 }
+}  // namespace
 
 // Smallest N that runs two-pass by default (measured on GB300: two passes
 // beat the cluster kernel from here up).
@@ -77,6 +79,7 @@ int effective_variant(lct_plan p) {
     return v >= 0 ? v : default_variant(p->dtype, p->desc[0].log2n);
 }
 
+namespace {
 // Two-pass path ------------------------------------------------------------
 // Workspace bytes of the two-pass path for `count` signals of N = 2^log2n:
 // the ring slots, then the queue and counters.
@@ -275,6 +278,7 @@ lct_status run_ragged(lct_plan p, const void* in, void* out, cudaStream_t stream
     }
     return from_cuda(cudaGraphLaunch(p->gexec, stream));
 }
+}  // namespace
 
 // The transform on the current device with the plan's state set up (lock
 // held).  desc: the descriptors of the launch's signals (the plan's, or a
@@ -330,6 +334,7 @@ lct_status debug_check(lct_plan plan, const void* out, int64_t count, cudaStream
     return v == LCT_DEV_TIMEOUT ? LCT_ERR_TIMEOUT : LCT_ERR_DEVICE;
 }
 
+namespace {
 // Host-buffer execution ----------------------------------------------------
 // Signals per chunk: about 32 MiB of samples, at least one signal (measured
 // on GB300 with 512 MiB each way: 16 MiB 3.62 ms, 32 MiB 3.46 ms, 64 MiB
@@ -363,6 +368,7 @@ lct_status ensure_host_state(lct_plan p, int64_t chunk) {
     return LCT_OK;
 }
 
+}  // namespace
 
 }  // namespace lcth
 

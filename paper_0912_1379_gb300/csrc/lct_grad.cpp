@@ -11,6 +11,7 @@
 
 namespace lcth {
 
+namespace {
 // Backward helpers ----------------------------------------------------------
 // Coefficients of (SA, SR, SG) in (dl/da, dl/db, dl/dd), see k_general.cu.
 void grad_coefs(const double* p, int64_t N, double* c) {
@@ -44,6 +45,8 @@ lct_status ensure_grad_state(lct_plan p, int64_t batch) {
     }
     return LCT_OK;
 }
+
+}  // namespace
 
 bool real_params(const lct_plan p) {
     for (int64_t s = 0; s < p->count; ++s) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 namespace lcth {
+namespace {
 
 // ---------------------------------------------------------------------------
 // double-double arithmetic (Dekker / Knuth error-free transformations)
@@ -95,14 +96,14 @@ void dd_to_turns128(dd t, uint64_t* hi, uint64_t* lo) {
     *lo = (uint64_t)q;
 }
 
+}  // namespace
+
 // Fractional part of a double (|v| moderate) as a 64-bit turn fraction.
 uint64_t double_to_turns64(double v) {
     uint64_t hi, lo;
     dd_to_turns128({v, 0.0}, &hi, &lo);
     return hi + (lo >> 63);
 }
-
-typedef std::complex<double> cplx;
 
 int ilog2_exact(int64_t N) {
     if (N < 2 || N > 65536) return -1;
@@ -112,6 +113,7 @@ int ilog2_exact(int64_t N) {
     return p;
 }
 
+namespace {
 // Re(x/y) of complex FP64 numbers, in double-double.
 dd dd_re_div(cplx x, cplx y) {
     dd num = dd_add(two_prod(x.real(), y.real()), two_prod(x.imag(), y.imag()));
@@ -128,6 +130,8 @@ bool symplectic(cplx a, cplx b, cplx c, cplx d) {
     double tol = 1e-9 * std::fmax(1.0, std::fmax(std::abs(ad), std::abs(bc)));
     return std::abs(ad - bc - 1.0) <= tol;
 }
+
+}  // namespace
 
 // Build the descriptor of one signal.  Returns LCT_OK or a validation error.
 lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {

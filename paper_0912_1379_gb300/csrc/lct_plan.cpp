@@ -24,6 +24,7 @@
 // autotune cache: (gpu name, dtype, log2n) -> variant
 // ---------------------------------------------------------------------------
 namespace lcth {
+namespace {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
@@ -61,6 +62,7 @@ void tune_load_locked() {
     std::fclose(f);
 }
 
+}  // namespace
 int tune_lookup(int dtype, int log2n) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_load_locked();
@@ -196,7 +198,9 @@ lct_status ensure_device(lct_plan p) {
 // Debug mode (LCT_DEBUG=1 in the environment, or lct_set_debug): every
 // lct_execute / lct_backward synchronises its stream, scans the outputs for
 // non-finite samples and reports the device status word.
+namespace {
 std::atomic<int> g_debug{-1};
+}  // namespace
 bool debug_on() {
     int v = g_debug.load();
     if (v < 0) {
