@@ -48,6 +48,12 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden symbol visibility; the declarations in
+ * this header are its exported interface. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 struct CUstream_st;
 typedef struct CUstream_st* lct_stream_t;   /* == cudaStream_t */
 
@@ -307,6 +313,10 @@ lct_status lct_selftest_timeout(int which, double limit_ms, lct_stream_t stream)
  * count). */
 lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_reim, int32_t world,
                          int32_t* owner, double* load);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

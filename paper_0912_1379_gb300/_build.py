@@ -1,7 +1,8 @@
 """In-tree build of the native library liblct.so for sm_103a.
 
 Each CUDA translation unit is compiled by nvcc, the host C++ by g++, in
-parallel; the objects are linked with cuFFT into
+parallel, with hidden symbol visibility (include/lct.h marks the exported
+C ABI); the objects are linked with cuFFT into
 paper_0912_1379_gb300/liblct.so.  A rebuild happens only when a source or
 header is newer than the library.
 """
@@ -60,14 +61,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     for src in cu:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               "--expt-relaxed-constexpr", *inc, "-c", src, "-o", obj]
+               "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr", *inc, "-c", src,
+               "-o", obj]
         if ptxas_verbose:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append((cmd, obj))
     for src in cpp:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-Wextra",
-               *inc, "-c", src, "-o", obj]
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-ffp-contract=off",
+               "-Wall", "-Wextra", *inc, "-c", src, "-o", obj]
         jobs.append((cmd, obj))
 
     def run(job):
