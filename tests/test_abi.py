@@ -4,6 +4,8 @@ No compute call is made here (no GPU)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -35,6 +37,24 @@ def test_exports_every_declared_symbol():
     lib = ctypes.CDLL(lct.library_path())
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_exports_only_the_c_abi():
+    """Hidden visibility: the internal launchers and host helpers are not
+    exported; every exported C (unmangled) function is declared in include/."""
+    lib = ctypes.CDLL(lct.library_path())
+    for internal in ("lct_launch_fused", "lct_launch_twopass", "lct_launch_gen",
+                     "lct_twiddle_table", "lct_make_desc_host"):
+        assert not hasattr(lib, internal), internal
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--defined-only", lct.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines()
+                if len(ln.split()) == 3 and ln.split()[1] == "T"}
+    c_names = {n for n in exported if not n.startswith("_")}
+    assert c_names == set(declared_functions()), sorted(c_names ^ set(declared_functions()))
 
 
 def test_status_strings():
