@@ -1,6 +1,9 @@
-// General single-CTA XFT kernel: forward or adjoint transform, rows or
-// columns, with optional parameter-gradient sums.  Used by lct_backward
-// (adjoint + gradients) and by the separable 2-D transform (columns).
+// General single-CTA XFT kernel (k_xft_gen): forward or adjoint transform,
+// rows or columns, with optional parameter-gradient sums.  Used by
+// lct_backward (adjoint + gradients) and by the separable 2-D transform.
+// Complex64 columns of uniform parameters run the persistent form
+// k_xft_cols (strips staged by cp.async, diagonal factors tabulated once per
+// CTA); the gradient finalisation is k_grad_finalize.
 //
 // Adjoint (Sec. 3: L = S1 F S2, so L^H = S2^H F^H S1^H): the input is
 // multiplied by conj(post-chirp) * scale, the DFT runs with the inverse sign
