@@ -382,10 +382,10 @@ def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
     peak, peak_kind = measured_peak()
     fwd_bytes, bwd_bytes = 32 * pts, 64 * pts     # see the docstring of the phases below
     phases = {
-        "forward": {"ms": f_ms, "kernels": "k_xft_fused<11, float> rows + k_xft_gen<11> columns",
+        "forward": {"ms": f_ms, "kernels": "k_xft_fused<11, float> rows + k_xft_cols<11, G=4> columns",
                     "algorithmic_bytes": fwd_bytes, "achieved_gbs": fwd_bytes / (f_ms * 1e-3) / 1e9},
-        "backward": {"ms": b_ms, "kernels": "k_xft_gen<11> adjoint+gradient columns, then rows; "
-                                            "two gradient finalize kernels",
+        "backward": {"ms": b_ms, "kernels": "k_xft_cols<11, G=4> adjoint+gradient columns, then k_xft_gen<11> "
+                                            "rows; two gradient finalize kernels",
                      "algorithmic_bytes": bwd_bytes, "achieved_gbs": bwd_bytes / (b_ms * 1e-3) / 1e9},
     }
     achieved = bwd_bytes / (b_ms * 1e-3) / 1e9
@@ -402,8 +402,8 @@ def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
                        "l2": "inputs larger than L2 (256 MiB per buffer), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "backward phase (two k_xft_gen launches: reads g, G, f, "
-                                   "writes h, 32 B/pt each)"},
+                         "kernel": "backward phase (k_xft_cols + k_xft_gen launches: each reads g, "
+                                   "G, f and writes h, 32 B/pt)"},
             "phases": phases,
             "gpu_launches": 6 * args.steps,
         }), flush=True)
