@@ -349,3 +349,101 @@ def test_hermite_zero_frft_converges_like_one_over_N(z):
         scaled.append(err * N)
     scaled = np.array(scaled)
     assert scaled.max() / scaled.min() < 1.1
+
+
+# --------------------------------------------------------------------------
+# group law of the LCT (Sec. 1: LCT(M2) LCT(M1) = LCT(M2 M1), up to the
+# metaplectic sign) on the discrete transform
+# --------------------------------------------------------------------------
+def _mat(p):
+    a, b, c, d = p
+    return np.array([[a, b], [c, d]], dtype=np.float64)
+
+
+# (a1, d1, b2, d2); b1 = s pi/4 makes the first output grid y_j = 4 b1 x_j / pi
+# equal to +-x_j, so the first output is a sample vector on the second input
+# grid.  a2 = b2 (1 - d1) / b1 then makes the composed b equal b2, so both
+# sides land on the same output points.
+GROUP_CASES = [(0.6, 1.3, -1.3, 0.8), (-1.1, 0.4, 0.7, -1.5),
+               (0.2, -0.9, 1.9, 0.3), (0.9, 0.5, -0.6, 1.7)]
+
+
+@pytest.mark.parametrize("s", [+1, -1])
+@pytest.mark.parametrize("case", GROUP_CASES)
+def test_group_law_on_gaussians(case, s):
+    """O.lct(O.lct(f, M1), M2) = +-O.lct(f, M2 M1) for chirped, shifted
+    Gaussians (well resolved, so the discretisation error is spectrally small).
+    s = -1: b1 = -pi/4, the first output grid is the reversed input grid
+    (y_j = -x_j = x_{N-1-j}), so the intermediate is reversed before the second
+    transform; with case 2 the first factor then has b < 0 and the product
+    b > 0, so a wrong branch of sqrt(2 pi i b) at b < 0 does not cancel."""
+    N = 512
+    a1, d1, b2, d2 = case
+    b1 = s * np.pi / 4
+    M1 = (a1, b1, (a1 * d1 - 1) / b1, d1)
+    a2 = b2 * (1 - d1) / b1
+    M2 = (a2, b2, (a2 * d2 - 1) / b2, d2)
+    M = _mat(M2) @ _mat(M1)
+    assert abs(np.linalg.det(M) - 1) < 1e-12 and abs(M[0, 1] - b2) < 1e-12
+    x = O.nodes(N)
+    f = C.gaussian(x, 0.5, 0.4, 0.2) * np.exp(0.3j * x * x)
+    G1 = O.lct(f, M1)
+    if s < 0:
+        G1 = G1[::-1]
+    lhs = O.lct(G1, M2)
+    rhs = O.lct(f, tuple(M.ravel()))
+    assert min(rel_l2(lhs, rhs), rel_l2(-lhs, rhs)) < 1e-12
+
+
+def test_group_law_fails_for_a_swapped_composition():
+    """The same check rejects the product taken in the wrong order (M1 M2), so
+    it does test how the two parameter sets compose."""
+    N = 512
+    a1, d1, b2, d2 = GROUP_CASES[0]
+    b1 = np.pi / 4
+    M1 = (a1, b1, (a1 * d1 - 1) / b1, d1)
+    a2 = b2 * (1 - d1) / b1
+    M2 = (a2, b2, (a2 * d2 - 1) / b2, d2)
+    x = O.nodes(N)
+    f = C.gaussian(x, 0.5, 0.4, 0.2) * np.exp(0.3j * x * x)
+    lhs = O.lct(O.lct(f, M1), M2)
+    wrong = tuple((_mat(M1) @ _mat(M2)).ravel())
+    rhs = O.lct(f, wrong)
+    assert min(rel_l2(lhs, rhs), rel_l2(-lhs, rhs)) > 1e-2
+
+
+def _gaussian_lct_branches_written_out(y, al, be, ga, a, b, d):
+    """The Gaussian integral of eq. (lctuno) for real parameters, alpha > 0,
+    with every square root written as modulus and argument:
+      1/sqrt(2 pi i b) = e^{-i sgn(b) pi/4} / sqrt(2 pi |b|)   (principal root),
+      sqrt(pi/A) = sqrt(pi/|A|) e^{-i arg(A)/2},  A = alpha - i a/(2b),
+      arg(A) = -arctan(a / (2 b alpha))  (Re A = alpha > 0).
+    The same phase term appears in eq. (exa1) as e^{(i/2) arctan(a/(2 alpha b))}."""
+    y = np.asarray(y, dtype=np.float64)
+    inv_root = np.exp(-1j * np.sign(b) * np.pi / 4) / np.sqrt(2 * np.pi * abs(b))
+    A = al - 1j * a / (2 * b)
+    sqrt_pi_over_A = np.sqrt(np.pi / abs(A)) * np.exp(0.5j * np.arctan(a / (2 * b * al)))
+    B = -2 * be - 1j * y / b
+    return inv_root * sqrt_pi_over_A * np.exp(B * B / (4 * A) - ga + 1j * d * y * y / (2 * b))
+
+
+@pytest.mark.parametrize("N,abcd,gauss", [
+    (512, (1.0, -2.0, -0.5, 2.0), (1.0, 2.0, 3.0)),        # Fig. 1 case with b -> -b
+    (1024, (1.0, -100.0, 0.0, 1.0), (2.0, 1.0, 3.0)),      # Fig. 2 (Fresnel) with b -> -b
+    (512, (-0.7, -1.4, (-0.7 * 0.9 - 1) / -1.4, 0.9), (0.6, -0.3, 0.2)),
+])
+def test_gaussian_at_negative_b_with_branches_written_out(N, abcd, gauss):
+    """b < 0: modulus and phase of the oracle's output against the closed form
+    whose roots are written as modulus and argument (independent of the complex
+    square root used by the oracle and by gaussian_lct)."""
+    a, b, c, d = abcd
+    al, be, ga = gauss
+    x = O.nodes(N)
+    G = O.lct(C.gaussian(x, al, be, ga), abcd)
+    y = O.output_grid(N, abcd).real
+    ref = _gaussian_lct_branches_written_out(y, al, be, ga, a, b, d)
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    assert np.abs(np.abs(G) - np.abs(ref)).max() < 1e-12 * np.abs(ref).max()
+    dphi = np.angle(G[big] / ref[big])
+    assert np.abs(dphi).max() < 1e-10
+    assert rel_l2(G, ref) < 1e-12
