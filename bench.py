@@ -87,11 +87,13 @@ def parse():
                     choices=["native", "split_bf16", "split_fp16", "fp16"],
                     help="native: FP32 fused kernel (headline); split_*/fp16: the DFT passes "
                          "on the tensor cores")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged", "fields2d", "backward"],
+    ap.add_argument("--workload", default="uniform",
+                    choices=["uniform", "ragged", "fields2d", "backward", "config0", "uniform1024"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
                          "instances in one graph launch; fields2d: separable 2-D LCT forward + "
                          "backward on 8 fields of 2048 x 2048; backward: lct_backward (adjoint "
-                         "+ per-signal parameter gradients) on the 16384 x N=4096 batch")
+                         "+ per-signal parameter gradients) on the 16384 x N=4096 batch; config0: "
+                         "12 x N=256 complex128 latency; uniform1024: 4096 x N=1024 (L2 flushed)")
     return ap.parse_args()
 
 
@@ -201,6 +203,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def timed_loop(torch, step, steps, stream, device_index, barrier, max_over_ranks, no_clocks=False):
+    """Time `steps` calls of step() with CUDA events on `stream` (barrier and
+    synchronize on both sides, max over ranks), sampling the SM clocks with
+    nvidia-smi during the timed region.  If the region lasts under a second,
+    the same launch loop continues for 1.5 s so that the clock record has
+    samples under load.  Returns (ms per step, clocks summary or None)."""
+    sampler = ClockSampler(device_index)
+    if not no_clocks:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1)) / steps
+    note = "timed region"
+    if t_wall1 - t_wall0 < 1.0 and not no_clocks:
+        t_end = time.time() + 1.5
+        while time.time() < t_end:
+            for _ in range(max(1, min(200, int(50.0 / max(ms, 1e-3))))):
+                step()
+            torch.cuda.synchronize()
+        t_wall1 = time.time()
+        note = "timed region + 1.5 s continuation of the same launch loop"
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+    if clocks is not None:
+        clocks["window"] = note
+    return ms, clocks
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
@@ -258,9 +298,48 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# shared pieces of the secondary arms
+# ---------------------------------------------------------------------------
+def rel_l2_rows(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    return np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+
+
+def accuracy_block(err, against):
+    err = np.atleast_1d(np.asarray(err, dtype=np.float64))
+    return {"rel_l2_max": float(err.max()), "rel_l2_median": float(np.median(err)),
+            "signals": int(err.size), "against": against}
+
+
+def flush_l2(torch, scratch):
+    """Write a buffer larger than L2 (129 MB), so the next launch reads its
+    inputs from HBM."""
+    scratch.add_(1)
+
+
+def per_step_flushed(torch, step, steps, stream, scratch, barrier, max_over_ranks):
+    """Mean of `steps` per-launch CUDA-event intervals on `stream`, with L2
+    flushed outside the timed intervals (for inputs that fit in L2)."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush_l2(torch, scratch)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    times = [e0.elapsed_time(e1) for e0, e1 in evs]
+    return max_over_ranks(sum(times) / steps), max_over_ranks(statistics.median(times))
+
+
+# ---------------------------------------------------------------------------
 # ragged workload: 20000 instances, N = 2^6..2^16, four kinds, one graph launch
 # ---------------------------------------------------------------------------
-def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     """The 20000-instance batch.  Under torchrun every rank builds the same
     global batch and transforms its share from lct_partition (cost-balanced,
     largest first): strong scaling, no collective on the data path."""
@@ -274,8 +353,8 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
     owner, load = lct.lct_partition(Ns, world, abcd)
     mine = np.nonzero(owner == rank)[0]
     offs = np.concatenate([[0], np.cumsum(Ns[mine])[:-1]]).astype(np.int64)
-    local = int(Ns[mine].sum())
-    buf = np.empty(local, dtype=np.complex64)
+    local_pts = int(Ns[mine].sum())
+    buf = np.empty(local_pts, dtype=np.complex64)
     rng = r["rng"]
     pos = {int(s): k for k, s in enumerate(mine)}
     for s in range(M):                       # the draw order defines the workload
@@ -290,26 +369,55 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()
     count = len(mine)
-    for _ in range(args.warmup):
+
+    def step():
         plan.execute(d_in, d_out, count, stream)
+
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
     if lct.lct_device_status(plan.handle) != 0:
         raise RuntimeError("device status after warm-up")
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        plan.execute(d_in, d_out, count, stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1)) / args.steps
-    plan.destroy()
+    ms, clocks = timed_loop(torch, step, args.steps, stream, local, barrier, max_over_ranks,
+                            args.no_clocks)
     total = int(Ns.sum())
     value = total / (ms * 1e-3)
     peak, peak_kind = measured_peak()
     achieved = total * BYTES_PER_POINT / world / (ms * 1e-3) / 1e9     # per GPU
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        # one signal of every (kind, N) owned here, N up to 32768: the oracle
+        # on those (bounded CPU time) and the GPU output against it
+        import oracle as O
+        O.build()
+        G = d_out.cpu().numpy()
+        errs, pts, t_cpu = [], 0, 0.0
+        kind_names = {W.KIND_GENERIC: "generic", W.KIND_FRFT: "frft", W.KIND_FOURIER: "fourier",
+                      W.KIND_B0: "b0"}
+        worst = {}
+        for kind in range(4):
+            for log2n in range(6, 16):
+                cand = [k for k, s in enumerate(mine) if r["kind"][s] == kind and r["log2n"][s] == log2n]
+                if not cand:
+                    continue
+                k = cand[0]
+                s = mine[k]
+                N = int(Ns[s])
+                f = buf[offs[k]:offs[k] + N].astype(np.complex128)
+                t0 = time.perf_counter()
+                ref = O.lct(f, abcd[s])
+                t_cpu += time.perf_counter() - t0
+                pts += N
+                e = float(rel_l2_rows(G[offs[k]:offs[k] + N], ref))
+                errs.append(e)
+                key = kind_names[kind]
+                worst[key] = max(worst.get(key, 0.0), e)
+        accuracy = accuracy_block(errs, "FP64 oracle, one signal of every (kind, N <= 32768)")
+        accuracy["rel_l2_max_by_kind"] = worst
+        cpu = {"value": pts / t_cpu, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": "one signal of every (kind, N = 64..32768) of the workload: %d signals, "
+                         "%d points, %.1f s (O(N^2) per signal)" % (len(errs), pts, t_cpu)}
+    plan.destroy()
     if rank == 0:
         by_n = {int(n): int((Ns == n).sum()) for n in np.unique(Ns)}
         print(json.dumps({
@@ -323,9 +431,13 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
                        "points": total, "signals_by_N": by_n,
                        "sharding": "lct_partition over %d ranks (cost N log2 N, largest first); "
                                    "load imbalance %.2e" % (world, load.max() / load.mean() - 1),
-                       "l2": "inputs larger than L2 (1.9 GB per buffer at one GPU)"},
+                       "l2": "inputs larger than L2 (1.9 GB per buffer at one GPU), no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "whole graph (one kernel per N group + b = 0 chunks), 16 B/point"},
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
             "gpu_launches": args.steps * n_groups,
         }), flush=True)
 
@@ -333,11 +445,13 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
 # ---------------------------------------------------------------------------
 # 2-D fields: forward + backward (input gradient and (a, b, d) per axis)
 # ---------------------------------------------------------------------------
-def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     """8 complex64 fields of 2048 x 2048 (Gaussian beam x bicubic phase
     screen).  One step = lct2d_execute (rows, then columns) + lct2d_backward
     (columns, then rows, each with the parameter-gradient sums) for a fixed
-    upstream gradient dl/dG of the intensity loss sum (|G|^2 - I)^2."""
+    upstream gradient dl/dG of the intensity loss sum (|G|^2 - I)^2.
+    Forward and backward are timed as two loops of their own (each clocked);
+    the step time is their sum."""
     B, n = 8, 2048
     x = lct.lct_input_grid(n)
     fields, ax, ay = W.fields_batch(x, B, seed=W.SEED_FIELDS + rank)
@@ -362,33 +476,59 @@ def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
         fwd()
         bwd()
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
-    barrier()
+    f_ms, f_clocks = timed_loop(torch, fwd, args.steps, stream, local, barrier, max_over_ranks,
+                                args.no_clocks)
+    b_ms, b_clocks = timed_loop(torch, bwd, args.steps, stream, local, barrier, max_over_ranks,
+                                args.no_clocks)
+    fwd()
     torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        fwd()
-        ev[2 * k + 1].record(stream)
-        bwd()
-        ev[2 * k + 2].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    f_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)) / args.steps
-    b_ms = sum(ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps)) / args.steps
-    f_ms, b_ms = max_over_ranks(f_ms), max_over_ranks(b_ms)
     ms = f_ms + b_ms
-    lct.lct2d_plan_destroy(plan)
     pts = B * n * n
     peak, peak_kind = measured_peak()
-    fwd_bytes, bwd_bytes = 32 * pts, 64 * pts     # see the docstring of the phases below
+    fwd_bytes, bwd_bytes = 32 * pts, 64 * pts
     phases = {
         "forward": {"ms": f_ms, "kernels": "k_xft_fused<11, float> rows + k_xft_cols<11, G=4> columns",
-                    "algorithmic_bytes": fwd_bytes, "achieved_gbs": fwd_bytes / (f_ms * 1e-3) / 1e9},
+                    "algorithmic_bytes": fwd_bytes, "achieved_gbs": fwd_bytes / (f_ms * 1e-3) / 1e9,
+                    "frac": fwd_bytes / (f_ms * 1e-3) / 1e9 / peak, "clocks": f_clocks},
         "backward": {"ms": b_ms, "kernels": "k_xft_cols<11, G=4> adjoint+gradient columns, then k_xft_gen<11> "
                                             "rows; two gradient finalize kernels",
-                     "algorithmic_bytes": bwd_bytes, "achieved_gbs": bwd_bytes / (b_ms * 1e-3) / 1e9},
+                     "algorithmic_bytes": bwd_bytes, "achieved_gbs": bwd_bytes / (b_ms * 1e-3) / 1e9,
+                     "frac": bwd_bytes / (b_ms * 1e-3) / 1e9 / peak, "clocks": b_clocks},
     }
     achieved = bwd_bytes / (b_ms * 1e-3) / 1e9
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        # each pass against the oracle on sampled lines: rows of the row
+        # pass (mid) from the input, columns of the column pass (out) from the
+        # GPU's own mid; the oracle rate on those 1-D transforms is the CPU
+        # baseline (a 2-D point needs two of them)
+        import oracle as O
+        O.build()
+        h_in, h_mid, h_out = xf.cpu().numpy(), mid.cpu().numpy(), out.cpu().numpy()
+        errs, pts_cpu, t_cpu = [], 0, 0.0
+        rng = np.random.default_rng(5)
+        k = 0
+        while (t_cpu < 10.0 and k < 256) or k < 16:
+            b = int(rng.integers(B))
+            line = int(rng.integers(n))
+            t0 = time.perf_counter()
+            if k % 2 == 0:
+                ref = O.lct(h_in[b, line, :].astype(np.complex128), ax)
+                got = h_mid[b, line, :]
+            else:
+                ref = O.lct(h_mid[b, :, line].astype(np.complex128), ay)
+                got = h_out[b, :, line]
+            t_cpu += time.perf_counter() - t0
+            pts_cpu += n
+            errs.append(float(rel_l2_rows(got, ref)))
+            k += 1
+        accuracy = accuracy_block(errs, "FP64 oracle on sampled rows (row pass) and columns "
+                                        "(column pass, from the GPU's row-pass output)")
+        rate_1d = pts_cpu / t_cpu
+        cpu = {"value": rate_1d / 2, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": "%d random rows/columns of 2048 (O(N^2) each), %.1f s; 2-D forward "
+                         "points/s = 1-D rate / 2 (forward only)" % (k, t_cpu)}
+    lct.lct2d_plan_destroy(plan)
     if rank == 0:
         print(json.dumps({
             "metric": "2-D LCT forward + backward points/s (8 x 2048 x 2048 complex64)",
@@ -405,6 +545,9 @@ def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
                          "kernel": "backward phase (k_xft_cols + k_xft_gen launches: each reads g, "
                                    "G, f and writes h, 32 B/pt)"},
             "phases": phases,
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": b_clocks,
             "gpu_launches": 6 * args.steps,
         }), flush=True)
 
@@ -412,7 +555,7 @@ def fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
 # ---------------------------------------------------------------------------
 # 1-D backward on the headline batch
 # ---------------------------------------------------------------------------
-def backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
+def backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     """One step = lct_backward of the 16384 x 4096 batch plan: grad_in =
     L^H g and (dl/da, dl/db, dl/dd) per signal (the adjoint kernel with the
     gradient sums reads g, f and G and writes grad_in: 32 B/point)."""
@@ -429,24 +572,42 @@ def backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
     gin = torch.empty_like(d_in)
     gp = torch.zeros(3 * count, dtype=torch.float64, device="cuda")
     res = {}
+    clocks = None
     for name, grad_abd, bpp in [("with_param_grads", gp, 32), ("adjoint_only", None, 16)]:
         def step():
             lct.lct_backward(plan.handle, g, d_in, d_out, gin, grad_abd, count, stream)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        ms, ck = timed_loop(torch, step, args.steps, stream, local, barrier, max_over_ranks,
+                            args.no_clocks)
+        if clocks is None:
+            clocks = ck
         res[name] = {"ms": ms, "algorithmic_bytes": bpp * count * N,
-                     "achieved_gbs": bpp * count * N / (ms * 1e-3) / 1e9}
+                     "achieved_gbs": bpp * count * N / (ms * 1e-3) / 1e9, "clocks": ck}
+    # leave the with-gradient results in gin and gp for the accuracy check
+    lct.lct_backward(plan.handle, g, d_in, d_out, gin, gp, count, stream)
+    torch.cuda.synchronize()
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        ks = 8
+        gg = g[:ks].cpu().numpy().astype(np.complex128)
+        ff = f[:ks].astype(np.complex128)
+        t0 = time.perf_counter()
+        h_ref = O.lct_adjoint(gg, params[:ks])
+        p_ref = O.lct_grad_params(ff, gg, params[:ks])
+        t_cpu = time.perf_counter() - t0
+        err_h = rel_l2_rows(gin[:ks].cpu().numpy(), h_ref)
+        p_got = gp[:3 * ks].cpu().numpy().reshape(ks, 3)
+        err_p = np.abs(p_got - p_ref).max(axis=1) / np.abs(p_ref).max(axis=1)
+        accuracy = accuracy_block(err_h, "FP64 oracle adjoint (grad_in) on the first %d signals" % ks)
+        accuracy["param_grad_rel_max"] = float(err_p.max())
+        accuracy["param_grad_against"] = "oracle dense-matrix gradient (max |error| / max |grad| per signal)"
+        cpu = {"value": ks * N / t_cpu, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": "first %d signals: O(N^2) adjoint + dense-matrix parameter gradient, %.1f s"
+                         % (ks, t_cpu)}
     plan.destroy()
     peak, peak_kind = measured_peak()
     main = res["with_param_grads"]
@@ -465,9 +626,153 @@ def backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks):
                          "peak_kind": peak_kind,
                          "kernel": "k_xft_gen<12, float, adjoint, gradient sums> (+ finalize)"},
             "phases": res,
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
             "gpu_launches": 2 * args.steps,
         }), flush=True)
 
+
+# ---------------------------------------------------------------------------
+# small configurations: 12 x 256 complex128 (latency) and 4096 x 1024
+# complex64 (fits in L2: flushed between launches)
+# ---------------------------------------------------------------------------
+def config0_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
+    """The FP64 case: the polynomial e^{-x^2/2}(1 + 0.3x + 0.1x^3) and the
+    Hermite functions psi_0..psi_10 (12 signals of N = 256, complex128),
+    rotation angle 0.7.  One step = one lct_execute; microseconds per batch
+    (launch and latency bound), L2 flushed between launches."""
+    N = 256
+    x = lct.lct_input_grid(N)
+    f = W.config0_signals(x)
+    abcd = W.config0_params()
+    B = f.shape[0]
+    plan = lct.Plan.create(N, *abcd, dtype=lct.LCT_C128)
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(f).cuda()
+    d_out = torch.empty_like(d_in)
+    scratch = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")    # 256 MiB > L2
+
+    def step():
+        plan.execute(d_in, d_out, B, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(args.steps, 50)
+    mean_ms, med_ms = per_step_flushed(torch, step, steps, stream, scratch, barrier, max_over_ranks)
+    _, clocks = timed_loop(torch, step, steps, stream, local, barrier, max_over_ranks, args.no_clocks)
+    G = d_out.cpu().numpy()
+    plain_us = None
+    if not args.no_plain:
+        pp = lct.Plan.create(N, *abcd, dtype=lct.LCT_C128).set_precision(lct.LCT_PREC_PLAIN64)
+        o2 = torch.empty_like(d_in)
+        for _ in range(3):
+            pp.execute(d_in, o2, B, stream)
+        pm, _ = per_step_flushed(torch, lambda: pp.execute(d_in, o2, B, stream), steps, stream,
+                                 scratch, barrier, max_over_ranks)
+        plain_us = pm * 1e3
+        pp.destroy()
+    accuracy = cpu = None
+    if rank == 0:
+        import oracle as O
+        O.build()
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            ref = O.lct(f, abcd)
+            reps += 1
+            if time.perf_counter() - t0 > 2.0:
+                break
+        t_cpu = (time.perf_counter() - t0) / reps
+        accuracy = accuracy_block(rel_l2_rows(G, ref), "FP64 oracle, all 12 signals")
+        if not args.no_cpu:
+            cpu = {"value": t_cpu * 1e6, "unit": "us per batch", "cores": O.num_threads(),
+                   "kind": "oracle", "sample": "the whole batch (12 x 256), %d repetitions" % reps}
+    plan.destroy()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "LCT latency, 12 x N=256 complex128 (FP64), rotation 0.7",
+            "value": mean_ms * 1e3, "unit": "us per batch", "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": mean_ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "config0: e^{-x^2/2}(1+0.3x+0.1x^3) + psi_0..psi_10, N=256, "
+                                   "complex128, (a,b,c,d) = rotation 0.7",
+                       "median_us": med_ms * 1e3,
+                       "l2": "L2 flushed (256 MiB write) before every timed launch",
+                       "kernel": "k_xft_fused<8, double, one signal per CTA>"},
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "plain64_us": plain_us,
+            "clocks": clocks,
+            "gpu_launches": steps,
+        }), flush=True)
+
+
+def uniform1024_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
+    """4096 complex64 signals of N = 1024, G1 per-signal parameters (seed
+    1001).  The 32 MiB input fits in L2, so L2 is flushed before every timed
+    launch; one step = one lct_execute."""
+    N, count = 1024, 4096
+    x = lct.lct_input_grid(N)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_1024 + rank, dtype=np.complex64)
+    plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(f).cuda()
+    d_out = torch.empty_like(d_in)
+    scratch = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
+    variant = plan.autotune(d_in, d_out, count, stream)
+
+    def step():
+        plan.execute(d_in, d_out, count, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    steps = max(args.steps, 50)
+    mean_ms, med_ms = per_step_flushed(torch, step, steps, stream, scratch, barrier, max_over_ranks)
+    _, clocks = timed_loop(torch, step, steps, stream, local, barrier, max_over_ranks, args.no_clocks)
+    G = d_out.cpu().numpy()
+    plains = {}
+    if not args.no_plain:
+        for name, prec in [("plain64", lct.LCT_PREC_PLAIN64), ("plain32", lct.LCT_PREC_PLAIN32)]:
+            pp = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N,
+                                dtype=lct.LCT_C64).set_precision(prec)
+            o2 = torch.empty_like(d_in)
+            for _ in range(3):
+                pp.execute(d_in, o2, count, stream)
+            pm, _ = per_step_flushed(torch, lambda: pp.execute(d_in, o2, count, stream), steps,
+                                     stream, scratch, barrier, max_over_ranks)
+            plains[name] = {"ms_per_step": pm, "value": world * count * N / (pm * 1e-3),
+                            "unit": "points/s"}
+            pp.destroy()
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, nsig, dt, cores, ref = cpu_oracle_rate(x, params, f)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d signals of the %d x N=%d workload, %.1f s" % (nsig, count, N, dt)}
+        accuracy = accuracy_block(rel_l2_rows(G[:nsig], ref), "FP64 oracle on the cpu_baseline sample")
+    plan.destroy()
+    peak, peak_kind = measured_peak()
+    achieved = count * N * BYTES_PER_POINT / (mean_ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "LCT points/s at N=1024 batched (4096 signals, complex64); %HBM",
+            "value": world * count * N / (mean_ms * 1e-3), "unit": "points/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "uniform batch 4096 x N=1024 complex64, G1 per-signal (a,b,c,d), "
+                                   "seed %d" % W.SEED_UNIFORM_1024,
+                       "median_ms": med_ms, "kernel_variant": variant,
+                       "l2": "L2 flushed (256 MiB write) before every timed launch"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_xft_fused<10, float> (variant %s)" % variant},
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "baselines": plains,
+            "clocks": clocks,
+            "gpu_launches": steps,
+        }), flush=True)
 
 # ---------------------------------------------------------------------------
 # our arm
@@ -500,12 +805,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    if args.workload == "ragged":
-        return ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
-    if args.workload == "fields2d":
-        return fields2d_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
-    if args.workload == "backward":
-        return backward_arm(args, rank, world, lct, torch, barrier, max_over_ranks)
+    arms = {"ragged": ragged_arm, "fields2d": fields2d_arm, "backward": backward_arm,
+            "config0": config0_arm, "uniform1024": uniform1024_arm}
+    if args.workload in arms:
+        arms[args.workload](args, rank, world, lct, torch, barrier, max_over_ranks, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     N, count = args.n, args.count
     x = lct.lct_input_grid(N)
     params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + rank, dtype=np.complex64)
@@ -536,38 +842,8 @@ def main():
     if status != 0:
         raise RuntimeError("device status %d after warm-up" % status)
 
-    sampler = ClockSampler(local)
-    if not args.no_clocks:
-        sampler.start()
-        time.sleep(0.3)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    barrier()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
-    ms_per_step = ms_total / args.steps
-    # Clock samples need ~1 s under load; if the K steps were shorter, the same
-    # launch loop continues for 1.5 s and the samples come from both.
-    clock_note = "timed region"
-    if t_wall1 - t_wall0 < 1.0 and not args.no_clocks:
-        t_end = time.time() + 1.5
-        while time.time() < t_end:
-            for _ in range(50):
-                step()
-            torch.cuda.synchronize()
-        t_wall1 = time.time()
-        clock_note = "timed region + 1.5 s continuation of the same launch loop"
-    clocks = sampler.summary(t_wall0, t_wall1)
-    sampler.stop()
-    if clocks is not None:
-        clocks["window"] = clock_note
+    ms_per_step, clocks = timed_loop(torch, step, args.steps, stream, local, barrier,
+                                     max_over_ranks, args.no_clocks)
 
     value = world * n_points / (ms_per_step * 1e-3)
     peak, peak_kind = measured_peak()
@@ -579,24 +855,32 @@ def main():
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}
 
-    # plain FP64 path on the same batch
-    plain = None
+    # the unfused paths on the same batch: FP64 (the named comparison) and FP32
+    plain = plain32 = None
     if not args.no_plain:
-        plan.set_precision(lct.LCT_PREC_PLAIN64)
-        for _ in range(3):
-            step()
+        for prec in (lct.LCT_PREC_PLAIN64, lct.LCT_PREC_PLAIN32):
+            plan.set_precision(prec)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+            if prec == lct.LCT_PREC_PLAIN64:
+                plain = {"value": world * n_points / (pms * 1e-3), "unit": "points/s",
+                         "ms_per_step": pms,
+                         "path": "chirp kernel + cuFFT Z2Z + chirp kernel, FP64 workspace"}
+            else:
+                plain32 = {"value": world * n_points / (pms * 1e-3), "unit": "points/s",
+                           "ms_per_step": pms,
+                           "path": "FP32 chirp kernel + cuFFT C2C + FP32 chirp kernel (unfused, "
+                                   "same arithmetic as the fused kernel)"}
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
-        plain = {"value": world * n_points / (pms * 1e-3), "unit": "points/s", "ms_per_step": pms,
-                 "path": "chirp kernel + cuFFT Z2Z + chirp kernel, FP64 workspace"}
-        torch.cuda.synchronize()
-        # release the plain path's workspace
+        # release the plain paths' workspace
         plan.destroy()
         plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
         if variant is None:
@@ -665,6 +949,8 @@ def main():
             "clocks": clocks,
             "plain64": plain,
             "speedup_vs_plain64": (plain["ms_per_step"] / ms_per_step) if plain else None,
+            "plain32": plain32,
+            "speedup_vs_plain32": (plain32["ms_per_step"] / ms_per_step) if plain32 else None,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -66,6 +66,10 @@ typedef enum { LCT_C64 = 0, LCT_C128 = 1 } lct_dtype;
  *              (FP32 for LCT_C64, FP64 for LCT_C128); phases exact (below).
  *  PLAIN64     unfused FP64 baseline: a chirp kernel, a library FFT (cuFFT
  *              Z2Z, forward sign) on an FP64 workspace, a chirp+scale kernel.
+ *  PLAIN32     unfused FP32 baseline (complex64 plans of one N; else
+ *              LCT_ERR_UNSUPPORTED): the same three steps in FP32 with cuFFT
+ *              C2C on an FP32 workspace -- the fused kernel's arithmetic
+ *              without the fusion.
  *  SPLIT_BF16, SPLIT_FP16, FP16
  *              tensor-core DFT (complex64 plans, one N in [16, 4096]): the
  *              radix-16 DFT passes run as real 32x32 DFT-matrix products
@@ -87,7 +91,8 @@ typedef enum {
     LCT_PREC_SPLIT_BF16 = 1,
     LCT_PREC_SPLIT_FP16 = 2,
     LCT_PREC_FP16 = 3,
-    LCT_PREC_PLAIN64 = 4
+    LCT_PREC_PLAIN64 = 4,
+    LCT_PREC_PLAIN32 = 5
 } lct_precision;
 
 typedef enum {
@@ -267,13 +272,19 @@ lct_status lct_plan_destroy(lct_plan plan);
  * loads the library holds until the process exits.
  * Limits: N a power of two in [2, LCT_NOALLOC_MAX_N], else LCT_ERR_N;
  * batch * N <= LCT_NOALLOC_MAX_POINTS, else LCT_ERR_ARG (nothing is run).
- * The first call on a device looks up the array's device address and sets
- * the DFT kernel's shared-memory limit (once per device); make that first
- * call before any stream capture.  All calls share the array: calls whose
- * kernels overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.  No state carries over between calls.
- * in/out as lct_execute (device buffers, in == out allowed); asynchronous on
- * `stream`. */
+ * The first call on a device (batch 0 is enough) looks up the array's device
+ * address, sets the DFT kernel's shared-memory limit and reads the
+ * multiprocessor count, once per device.  Under CUDA's lazy module loading
+ * that first call is also when the 32 MiB array is committed on the device,
+ * so make it before the caller's pool reserves the device memory, and before
+ * any stream capture.  The per-device set-up is not redone after
+ * cudaDeviceReset: do not use this entry point across a device reset.  If a
+ * CUDA error is already pending on the calling thread, the call returns
+ * LCT_ERR_CUDA without launching and leaves that error pending.  All calls
+ * share the array: calls whose kernels overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  No state
+ * carries over between calls.  in/out as lct_execute (device buffers, in ==
+ * out allowed); asynchronous on `stream`. */
 #define LCT_NOALLOC_MAX_N 4096
 #define LCT_NOALLOC_MAX_POINTS (1 << 21)
 lct_status lct_execute_noalloc(int64_t N, double a, double b, double c, double d,

@@ -18,7 +18,8 @@ import numpy as np
 from . import _build
 
 LCT_C64, LCT_C128 = 0, 1
-LCT_PREC_NATIVE, LCT_PREC_SPLIT_BF16, LCT_PREC_SPLIT_FP16, LCT_PREC_FP16, LCT_PREC_PLAIN64 = range(5)
+(LCT_PREC_NATIVE, LCT_PREC_SPLIT_BF16, LCT_PREC_SPLIT_FP16, LCT_PREC_FP16, LCT_PREC_PLAIN64,
+ LCT_PREC_PLAIN32) = range(6)
 STATUS = ["LCT_OK", "LCT_ERR_ARG", "LCT_ERR_N", "LCT_ERR_NOT_SYMPLECTIC", "LCT_ERR_DTYPE",
           "LCT_ERR_ALIGN", "LCT_ERR_OOM", "LCT_ERR_CUDA", "LCT_ERR_DEVICE", "LCT_ERR_TIMEOUT",
           "LCT_ERR_UNSUPPORTED"]

@@ -12,30 +12,35 @@ namespace {
 
 using namespace xft;
 
-template <int L>
+// ONE = false: several signals per CTA for small N (256 threads);
+// ONE = true: one signal per CTA, for batches too small to give every SM a
+// CTA of packed signals (latency: FP64 work spread over more SMs).
+template <int L, bool ONE = false>
 struct fused_shape {
     static constexpr int T = shape<L>::T;
-    static constexpr int SPC = T >= 256 ? 1 : 256 / T;     // signals per CTA
+    static constexpr int SPC = (T >= 256 || ONE) ? 1 : 256 / T;     // signals per CTA
     static constexpr int THREADS = T * SPC;
 };
 
 // Minimum resident CTAs per SM for __launch_bounds__: keeps FP32 kernels at
 // <= 64 registers (1024 resident threads fill the 64K register file) and
 // FP64 kernels at <= 128 (512 resident threads).
-template <int L, class R>
+template <int L, class R, bool ONE = false>
 constexpr int min_blocks() {
     constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
-    return per_sm / fused_shape<L>::THREADS > 0 ? per_sm / fused_shape<L>::THREADS : 1;
+    constexpr int th = fused_shape<L, ONE>::THREADS;
+    constexpr int b = per_sm / th > 0 ? per_sm / th : 1;
+    return b > 32 ? 32 : b;
 }
 
-template <int L, class R>
-__global__ void __launch_bounds__(fused_shape<L>::THREADS, (min_blocks<L, R>()))
+template <int L, class R, bool ONE>
+__global__ void __launch_bounds__(fused_shape<L, ONE>::THREADS, (min_blocks<L, R, ONE>()))
 k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
             const lct_desc* __restrict__ desc, int desc_step, int64_t count,
             const cpx<R>* __restrict__ tw, const int32_t* __restrict__ idx,
             int32_t* __restrict__ status) {
     using S = shape<L>;
-    using F = fused_shape<L>;
+    using F = fused_shape<L, ONE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
     const int tid = threadIdx.x;
@@ -201,14 +206,14 @@ cudaError_t launch_tma(const void* in, void* out, const lct_desc* desc, int desc
     return cudaGetLastError();
 }
 
-template <int L, class R>
-cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc_step,
-                       int64_t count, const void* tw, const int32_t* idx, int32_t* status,
-                       cudaStream_t stream) {
+template <int L, class R, bool ONE>
+cudaError_t launch_shape(const void* in, void* out, const lct_desc* desc, int desc_step,
+                         int64_t count, const void* tw, const int32_t* idx, int32_t* status,
+                         cudaStream_t stream) {
     using S = shape<L>;
-    using F = fused_shape<L>;
+    using F = fused_shape<L, ONE>;
     const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
-    auto kern = k_xft_fused<L, R>;
+    auto kern = k_xft_fused<L, R, ONE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -219,6 +224,35 @@ cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc
     kern<<<(unsigned)blocks, F::THREADS, smem, stream>>>(
         (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, (const cpx<R>*)tw, idx, status);
     return cudaGetLastError();
+}
+
+// Multiprocessors of the current device (cached per device).
+int sm_count() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
+
+// Packed signals per CTA, unless that leaves SMs idle: then one signal per
+// CTA, so that a small batch (the 12-signal FP64 case, say) runs on as many
+// SMs as it has signals.
+template <int L, class R>
+cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc_step,
+                       int64_t count, const void* tw, const int32_t* idx, int32_t* status,
+                       cudaStream_t stream) {
+    if constexpr (fused_shape<L>::SPC > 1) {
+        const int64_t packed = (count + fused_shape<L>::SPC - 1) / fused_shape<L>::SPC;
+        if (packed < sm_count())
+            return launch_shape<L, R, true>(in, out, desc, desc_step, count, tw, idx, status,
+                                            stream);
+    }
+    return launch_shape<L, R, false>(in, out, desc, desc_step, count, tw, idx, status, stream);
 }
 
 template <class R>

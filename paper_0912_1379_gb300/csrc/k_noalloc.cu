@@ -16,6 +16,12 @@
 // GPU (different streams, or different host threads) race on it.  Nothing
 // in it has to start at zero: every sample a call reads was written earlier
 // in the same call.
+//
+// When the memory is committed: with CUDA's lazy module loading this file's
+// module, and with it the array, is loaded on the first call on a device
+// (the symbol lookup in setup_device).  That first call -- a call with
+// batch 0 is enough -- should therefore come before the caller reserves its
+// device memory, and before any stream capture.
 #include "lct_internal.h"
 #include "xft_common.cuh"
 #include "../../include/lct.h"
@@ -29,6 +35,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_work_ptr[kMaxDevices] = {};   // device address of g_noalloc_work, per device
+int g_sm_count[kMaxDevices] = {};     // multiprocessors of each device (grid sizing)
 
 __global__ void k_na_pre(const void* __restrict__ in_, int dtype, cpx<double>* __restrict__ work,
                          lct_desc D, int64_t total, int log2n) {
@@ -105,9 +112,11 @@ __global__ void k_na_post(const cpx<double>* __restrict__ work, void* __restrict
 }
 
 // First call on a device: look up the array's device address (the host-side
-// name g_noalloc_work is only a stand-in and must never reach a kernel) and
-// allow the DFT kernel its shared memory.
-lct_status setup_device(cpx<double>** work) {
+// name g_noalloc_work is only a stand-in and must never reach a kernel),
+// allow the DFT kernel its shared memory and read the multiprocessor count.
+// The cache is keyed by device ordinal, so it does not survive
+// cudaDeviceReset (documented in include/lct.h).
+lct_status setup_device(cpx<double>** work, int* sms) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LCT_ERR_CUDA;
     std::lock_guard<std::mutex> g(g_setup_mu);
@@ -117,15 +126,23 @@ lct_status setup_device(cpx<double>** work) {
         if (cudaFuncSetAttribute(k_na_dft, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2 * LCT_NOALLOC_MAX_N * sizeof(cpx<double>))) != cudaSuccess)
             return LCT_ERR_CUDA;
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            return LCT_ERR_CUDA;
+        g_sm_count[dev] = n;
         g_work_ptr[dev] = p;
     }
     *work = (cpx<double>*)g_work_ptr[dev];
+    *sms = g_sm_count[dev];
     return LCT_OK;
 }
 
-unsigned grid_for(int64_t total) {
+// Grid of the grid-stride kernels: one 256-thread block per 256 samples, at
+// most 16 resident blocks per multiprocessor.
+unsigned grid_for(int64_t total, int sms) {
+    const int64_t cap = (int64_t)sms * 16;
     int64_t b = (total + 255) / 256;
-    return (unsigned)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 }  // namespace
@@ -137,26 +154,35 @@ extern "C" lct_status lct_execute_noalloc(int64_t N, double a, double b, double 
     if (N < 2 || N > LCT_NOALLOC_MAX_N || (N & (N - 1)) != 0) return LCT_ERR_N;
     if (batch < 0) return LCT_ERR_ARG;
     if (batch > LCT_NOALLOC_MAX_POINTS / N) return LCT_ERR_ARG;   // beyond the static array
-    if (batch == 0) return LCT_OK;
-    const uintptr_t align = dtype == LCT_C64 ? 8 : 16;
-    if (!in || !out) return LCT_ERR_ARG;
-    if (((uintptr_t)in) % align || ((uintptr_t)out) % align) return LCT_ERR_ALIGN;
     const double p[8] = {a, 0.0, b, 0.0, c, 0.0, d, 0.0};
     lct_desc D;
     lct_status st = (lct_status)lct_make_desc_host(N, p, 0, &D);
     if (st != LCT_OK) return st;
+    // Set-up first, also for batch 0: that call commits the array (module
+    // load) without running anything.
     cpx<double>* work = nullptr;
-    st = setup_device(&work);
+    int sms = 0;
+    st = setup_device(&work, &sms);
     if (st != LCT_OK) return st;
+    if (batch == 0) return LCT_OK;
+    const uintptr_t align = dtype == LCT_C64 ? 8 : 16;
+    if (!in || !out) return LCT_ERR_ARG;
+    if (((uintptr_t)in) % align || ((uintptr_t)out) % align) return LCT_ERR_ALIGN;
+    // An error left pending by earlier work on this thread is reported as
+    // LCT_ERR_CUDA without launching and is not cleared, so the caller can
+    // still read it; after that, an error is this call's own launch failure.
+    if (cudaPeekAtLastError() != cudaSuccess) return LCT_ERR_CUDA;
     cudaStream_t stream = (cudaStream_t)stream_;
     int log2n = 0;
     while ((int64_t(1) << log2n) < N) ++log2n;
     const int64_t total = batch * N;
-    k_na_pre<<<grid_for(total), 256, 0, stream>>>(in, dtype, work, D, total, log2n);
+    k_na_pre<<<grid_for(total, sms), 256, 0, stream>>>(in, dtype, work, D, total, log2n);
+    if (cudaGetLastError() != cudaSuccess) return LCT_ERR_CUDA;
     if (D.kind != LCT_KIND_DIAG) {
         const int threads = N >= 512 ? 256 : (int)(N / 2 > 32 ? N / 2 : 32);
         k_na_dft<<<(unsigned)batch, threads, 2 * N * sizeof(cpx<double>), stream>>>(work, log2n);
+        if (cudaGetLastError() != cudaSuccess) return LCT_ERR_CUDA;
     }
-    k_na_post<<<grid_for(total), 256, 0, stream>>>(work, out, dtype, D, total, log2n);
+    k_na_post<<<grid_for(total, sms), 256, 0, stream>>>(work, out, dtype, D, total, log2n);
     return cudaGetLastError() == cudaSuccess ? LCT_OK : LCT_ERR_CUDA;
 }

@@ -139,6 +139,48 @@ __global__ void k_plain_post(const cpx<double>* __restrict__ work, cpx<R>* __res
     }
 }
 
+// Plain FP32 path (complex64 plans): the same two chirp kernels in FP32 with
+// the 64-bit phase words, around a single-precision library FFT (C2C), so
+// that the fused kernel can be compared with an unfused path of the same
+// arithmetic precision.
+__global__ void k_plain_pre32(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ work,
+                              const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+                              int log2n) {
+    const int64_t N = 1ll << log2n;
+    const int64_t total = count * N;
+    const uint32_t cen = (uint32_t)((N - 1) << (31 - log2n));      // (N-1)/(2N) turns
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sig = t >> log2n;
+        const int n = (int)(t & (N - 1));
+        const lct_desc& D = desc[desc_step ? sig : 0];
+        const int64_t base = desc_step ? D.offset : sig * N;
+        const uint32_t m2 = m_squared(n, (int)N);
+        cpx<float> w = expi_turn32<true>(phase32(D.in_hi, m2) + (uint32_t)n * cen);
+        if (D.flags & LCT_FLAG_DECAY) w = cscale(w, expf(-(float)D.decay * (float)m2));
+        work[t] = cmul(in[base + n], w);
+    }
+}
+
+__global__ void k_plain_post32(const cpx<float>* __restrict__ work, cpx<float>* __restrict__ out,
+                               const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+                               int log2n) {
+    const int64_t N = 1ll << log2n;
+    const int64_t total = count * N;
+    const uint32_t cen = (uint32_t)((N - 1) << (31 - log2n));
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sig = t >> log2n;
+        const int n = (int)(t & (N - 1));
+        const lct_desc& D = desc[desc_step ? sig : 0];
+        const int64_t base = desc_step ? D.offset : sig * N;
+        const uint32_t m2 = m_squared(n, (int)N);
+        const uint32_t off = (uint32_t)((D.out_c + 0x80000000ull) >> 32);
+        cpx<float> w = expi_turn32<true>(phase32(D.out_hi, m2) + (uint32_t)n * cen + off);
+        out[base + n] = cscale(cmul(work[t], w), (float)D.scale);
+    }
+}
+
 unsigned grid_for(int64_t total, int threads) {
     int64_t b = (total + threads - 1) / threads;
     const int64_t cap = 152 * 32;  // grid-stride beyond this
@@ -218,5 +260,21 @@ cudaError_t lct_launch_plain_post(int dtype, int log2n, const void* work, void* 
     else
         k_plain_post<double><<<grid_for(total, th), th, 0, stream>>>(
             (const cpx<double>*)work, (cpx<double>*)out, desc, desc_step, count, log2n);
+    return cudaGetLastError();
+}
+
+cudaError_t lct_launch_plain32_pre(const void* in, void* work, const lct_desc* desc, int log2n,
+                                   int desc_step, int64_t count, cudaStream_t stream) {
+    const int64_t total = count << log2n;
+    k_plain_pre32<<<grid_for(total, 256), 256, 0, stream>>>(
+        (const cpx<float>*)in, (cpx<float>*)work, desc, desc_step, count, log2n);
+    return cudaGetLastError();
+}
+
+cudaError_t lct_launch_plain32_post(const void* work, void* out, const lct_desc* desc, int log2n,
+                                    int desc_step, int64_t count, cudaStream_t stream) {
+    const int64_t total = count << log2n;
+    k_plain_post32<<<grid_for(total, 256), 256, 0, stream>>>(
+        (const cpx<float>*)work, (cpx<float>*)out, desc, desc_step, count, log2n);
     return cudaGetLastError();
 }

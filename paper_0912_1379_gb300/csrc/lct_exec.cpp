@@ -15,12 +15,14 @@
 namespace lcth {
 
 namespace {
-// Plain FP64 path: chirp kernel -> cuFFT Z2Z (forward) -> chirp+scale kernel.
+// Plain paths: chirp kernel -> cuFFT (forward) -> chirp+scale kernel, on an
+// FP64 workspace with Z2Z (PLAIN64) or an FP32 one with C2C (PLAIN32).
 lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int desc_step,
                      cudaStream_t stream) {
+    const bool fp32 = p->prec == LCT_PREC_PLAIN32;
     int64_t N = p->N0;
     int log2n = p->desc[0].log2n;
-    size_t need = (size_t)count * (size_t)N * 16;
+    size_t need = (size_t)count * (size_t)N * (fp32 ? 8 : 16);
     if (need > p->work_bytes) {
         cudaFree(p->d_work);
         p->d_work = nullptr;
@@ -28,18 +30,29 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
         if (cudaMalloc(&p->d_work, need) != cudaSuccess) return LCT_ERR_OOM;
         p->work_bytes = need;
     }
-    if (!p->fft_valid || p->fft_n != N || p->fft_batch != count) {
+    const cufftType type = fp32 ? CUFFT_C2C : CUFFT_Z2Z;
+    if (!p->fft_valid || p->fft_n != N || p->fft_batch != count || p->fft_type != (int)type) {
         if (p->fft_valid) cufftDestroy(p->fft);
         p->fft_valid = false;
         int n = (int)N;
-        if (cufftPlanMany(&p->fft, 1, &n, nullptr, 1, n, nullptr, 1, n, CUFFT_Z2Z, (int)count) !=
+        if (cufftPlanMany(&p->fft, 1, &n, nullptr, 1, n, nullptr, 1, n, type, (int)count) !=
             CUFFT_SUCCESS)
             return LCT_ERR_CUDA;
         p->fft_valid = true;
         p->fft_n = N;
         p->fft_batch = count;
+        p->fft_type = (int)type;
     }
     if (cufftSetStream(p->fft, stream) != CUFFT_SUCCESS) return LCT_ERR_CUDA;
+    if (fp32) {
+        lct_status st = from_cuda(lct_launch_plain32_pre(in, p->d_work, p->d_desc, log2n,
+                                                         desc_step, count, stream));
+        if (st != LCT_OK) return st;
+        cufftComplex* w = (cufftComplex*)p->d_work;
+        if (cufftExecC2C(p->fft, w, w, CUFFT_FORWARD) != CUFFT_SUCCESS) return LCT_ERR_CUDA;
+        return from_cuda(lct_launch_plain32_post(p->d_work, out, p->d_desc, log2n, desc_step,
+                                                 count, stream));
+    }
     lct_status st = from_cuda(lct_launch_plain_pre(p->dtype, log2n, in, p->d_work, p->d_desc,
                                                    desc_step, count, stream));
     if (st != LCT_OK) return st;
@@ -300,7 +313,7 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
     if (D0.kind == LCT_KIND_DIAG)
         return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
                                          batch, nullptr, plan->d_status, stream));
-    if (plan->prec == LCT_PREC_PLAIN64) {
+    if (plan->prec == LCT_PREC_PLAIN64 || plan->prec == LCT_PREC_PLAIN32) {
         // the plain path assumes contiguous rows
         if (plan->is_batch && !plan->contiguous) return LCT_ERR_UNSUPPORTED;
         return run_plain(plan, in, out, batch, desc_step, stream);

@@ -204,3 +204,8 @@ cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* wor
 cudaError_t lct_launch_plain_post(int dtype, int log2n, const void* work, void* out,
                                   const lct_desc* desc, int desc_step, int64_t count,
                                   cudaStream_t stream);
+// Plain FP32 baseline pieces (complex64 in/out).  work: complex64 [count][N].
+cudaError_t lct_launch_plain32_pre(const void* in, void* work, const lct_desc* desc, int log2n,
+                                   int desc_step, int64_t count, cudaStream_t stream);
+cudaError_t lct_launch_plain32_post(const void* work, void* out, const lct_desc* desc, int log2n,
+                                    int desc_step, int64_t count, cudaStream_t stream);

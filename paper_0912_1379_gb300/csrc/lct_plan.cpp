@@ -346,6 +346,11 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
         case LCT_PREC_PLAIN64:
             plan->prec = precision;
             return LCT_OK;
+        case LCT_PREC_PLAIN32:
+            // FP32 chirps around cuFFT C2C: complex64 plans of one N
+            if (plan->dtype != LCT_C64 || plan->ragged || plan->N0 == 0) return LCT_ERR_UNSUPPORTED;
+            plan->prec = precision;
+            return LCT_OK;
         case LCT_PREC_SPLIT_BF16:
         case LCT_PREC_SPLIT_FP16:
         case LCT_PREC_FP16: {

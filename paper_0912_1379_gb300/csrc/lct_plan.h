@@ -41,6 +41,7 @@ struct lct_plan_s {
     cufftHandle fft = 0;
     bool fft_valid = false;
     int64_t fft_n = 0, fft_batch = 0;
+    int fft_type = 0;
     int variant = -1;               // -1: not chosen (cache or default 0)
     // ragged execution (mixed N or kinds): groups of equal (N, kind), largest
     // N first, each an index list into desc; run as one CUDA graph

@@ -218,6 +218,50 @@ def test_plain64_complex64_io():
     assert rel_l2(G, ref).max() < 1e-6
 
 
+@pytest.mark.parametrize("N", [256, 4096])
+def test_plain32_complex64(N):
+    """The unfused FP32 baseline (FP32 chirps around cuFFT C2C)."""
+    count = 16
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=19, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N).set_precision(lct.LCT_PREC_PLAIN32)
+    try:
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(np.complex128), params)
+    assert rel_l2(G, ref).max() < TOL32
+
+
+def test_plain32_rejects_complex128():
+    p = lct.Plan.create(256, 1.0, 2.0, 0.5, 2.0, dtype=lct.LCT_C128)
+    try:
+        with pytest.raises(lct.LctError) as e:
+            p.set_precision(lct.LCT_PREC_PLAIN32)
+        assert e.value.status == 10
+    finally:
+        p.destroy()
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("count", [1, 12, 16 * 160 + 3])
+def test_small_and_packed_batches_n256(dtype, count):
+    """N = 256 packs 16 signals per CTA; a batch that would fill fewer CTAs
+    than the GPU has SMs runs one signal per CTA instead (12 signals: the
+    complex128 latency case).  Both shapes against the oracle."""
+    N = 256
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=23 + count, dtype=np.complex128)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code)
+    try:
+        G = run(p.handle, f.astype(dtype), dtype)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(dtype).astype(np.complex128), params)
+    assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64)
+
+
 # --------------------------------------------------------------------------
 # b = 0 branch, complex parameters, fractional transform
 # --------------------------------------------------------------------------
@@ -445,16 +489,22 @@ def test_ragged_full_size_workload():
         G = out.cpu().numpy()
     finally:
         p.destroy()
-    # sample: a few signals of every kind, small and mid sizes
+    # sample: the first three signals of every kind at every N = 2^6 .. 2^16
+    # (the sizes from 8192 up hold most of the points; they run on the
+    # two-pass and single-CTA kernels of the graph, complex-z FrFT included)
     checked = 0
     for kind in range(4):
-        ids = [s for s in np.nonzero(r["kind"] == kind)[0] if Ns[s] <= 4096][:6]
-        for s in ids:
-            o, N = offs[s], Ns[s]
-            ref = O.lct(buf[o:o + N].astype(np.complex128), abcd[s])
-            assert rel_l2(G[o:o + N], ref) < TOL32, (kind, N)
-            checked += 1
-    assert checked >= 20
+        for log2n in range(6, 17):
+            ids = np.nonzero((r["kind"] == kind) & (r["log2n"] == log2n))[0][:3]
+            assert len(ids) == 3, (kind, log2n)
+            N = 1 << log2n
+            f = np.stack([buf[offs[s]:offs[s] + N] for s in ids]).astype(np.complex128)
+            ref = O.lct(f, abcd[ids])
+            for k, s in enumerate(ids):
+                o = offs[s]
+                assert rel_l2(G[o:o + N], ref[k]) < TOL32, (kind, N, int(s))
+                checked += 1
+    assert checked == 4 * 11 * 3
     # scaled Parseval for every real-parameter signal with b != 0
     for s in np.nonzero((r["kind"] == W.KIND_GENERIC) | (r["kind"] == W.KIND_FOURIER))[0]:
         o, N = offs[s], Ns[s]
