@@ -447,3 +447,25 @@ def test_gaussian_at_negative_b_with_branches_written_out(N, abcd, gauss):
     dphi = np.angle(G[big] / ref[big])
     assert np.abs(dphi).max() < 1e-10
     assert rel_l2(G, ref) < 1e-12
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_eigenvectors_match_recurrence_in_high_precision(N):
+    """Every column of U (signs included) equals the normalised vector
+    (p_0(x_k), ..., p_{N-1}(x_k)), p_n = H_n / sqrt(2^n n!), evaluated at the
+    oracle's nodes in 50-digit arithmetic: eq. (ortvec) up to its positive
+    normalisation (the sign factor (-1)^{N+k} / H_{N-1}(x_k) is positive).
+    Edge columns, whose first components are far below 1e-16, pin the sign
+    rule where a first-component test cannot."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    x, U = H.hermite_zero_basis(N)
+    ks = sorted(set([0, 1, 2, N // 4, N // 2, N - 3, N - 2, N - 1]))
+    for k in ks:
+        xx = mpmath.mpf(x[k])
+        p = [mpmath.mpf(1), mpmath.sqrt(2) * xx]
+        for n in range(1, N - 1):
+            p.append((mpmath.sqrt(2) * xx * p[-1] - mpmath.sqrt(n) * p[-2]) / mpmath.sqrt(n + 1))
+        norm = mpmath.sqrt(mpmath.fsum(v * v for v in p[:N]))
+        ref = np.array([float(v / norm) for v in p[:N]])
+        assert np.abs(U[:, k] - ref).max() < 1e-12, k
