@@ -88,12 +88,14 @@ def parse():
                     help="native: FP32 fused kernel (headline); split_*/fp16: the DFT passes "
                          "on the tensor cores")
     ap.add_argument("--workload", default="uniform",
-                    choices=["uniform", "ragged", "fields2d", "backward", "config0", "uniform1024"],
+                    choices=["uniform", "ragged", "fields2d", "backward", "config0", "uniform1024",
+                             "hermite"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
                          "instances in one graph launch; fields2d: separable 2-D LCT forward + "
                          "backward on 8 fields of 2048 x 2048; backward: lct_backward (adjoint "
                          "+ per-signal parameter gradients) on the 16384 x N=4096 batch; config0: "
-                         "12 x N=256 complex128 latency; uniform1024: 4096 x N=1024 (L2 flushed)")
+                         "12 x N=256 complex128 latency; uniform1024: 4096 x N=1024 (L2 flushed); "
+                         "hermite: the Hermite-zero FrFT of eq. (tmat), 4096 x N=1024")
     return ap.parse_args()
 
 
@@ -775,6 +777,85 @@ def uniform1024_arm(args, rank, world, lct, torch, barrier, max_over_ranks, loca
         }), flush=True)
 
 # ---------------------------------------------------------------------------
+# Hermite-zero discrete fractional transform (Sec. 2, eq. (tmat))
+# ---------------------------------------------------------------------------
+FP64_NOMINAL_TFLOPS = 1.25            # GB300 FP64 (nominal, CUDA cores)
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def hermite_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
+    """F_z = sqrt(2 pi) U^T D(z) U applied to a batch of signals sampled at
+    the zeros of H_N: two real-by-complex products of N x N by N x batch
+    (8 N^2 flops per signal), FP64 for complex128 (the headline of this arm)
+    and FP32 for complex64.  The basis is built once before timing."""
+    N, B = 1024, 4096
+    z = np.exp(-0.7j)
+    x, _ = lct.frft_hermite_basis(N, with_matrix=False)
+    rng = W.rng_for(W.SEED_UNIFORM_1024 + 17 + rank)
+    env = np.exp(-x * x / 6.0)
+    f = (env * (rng.standard_normal((B, N)) + 1j * rng.standard_normal((B, N)))).astype(np.complex128)
+    stream = torch.cuda.current_stream()
+    res = {}
+    clocks = None
+    outs = {}
+    for name, dt, code in [("c128", np.complex128, lct.LCT_C128), ("c64", np.complex64, lct.LCT_C64)]:
+        d_in = torch.from_numpy(f.astype(dt)).cuda()
+        d_out = torch.empty_like(d_in)
+
+        def step():
+            lct.frft_hermite_execute(N, z, d_in, d_out, B, code, stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 10)) if name == "c128" else args.steps
+        ms, ck = timed_loop(torch, step, steps, stream, local, barrier, max_over_ranks, args.no_clocks)
+        flops = 8.0 * N * N * B
+        peak = FP64_NOMINAL_TFLOPS if name == "c128" else FP32_DERIVED_TFLOPS
+        res[name] = {"ms": ms, "steps": steps, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak, "clocks": ck}
+        if clocks is None:
+            clocks = ck
+        outs[name] = d_out[:64].cpu().numpy()
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import hermite as H
+        t0 = time.perf_counter()
+        _, F = H.hermite_zero_frft(N, z)
+        ref = f[:64] @ F.T
+        t_cpu = time.perf_counter() - t0
+        e64 = rel_l2_rows(outs["c128"], ref)
+        e32 = rel_l2_rows(outs["c64"], f[:64].astype(np.complex64).astype(np.complex128) @ F.T)
+        accuracy = accuracy_block(e64, "oracle B (eigensolver basis, dense F_z), first 64 signals, complex128")
+        accuracy["complex64_rel_l2_max"] = float(e32.max())
+        cpu = {"value": 64 * N / t_cpu, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "oracle B: tridiagonal eigensolver + dense F_z (N = %d) + 64 signals, %.2f s"
+                         % (N, t_cpu)}
+    main = res["c128"]
+    if rank == 0:
+        print(json.dumps({
+            "metric": "Hermite-zero discrete FrFT (eq. tmat) points/s, N=1024, complex128 (FP64)",
+            "value": world * B * N / (main["ms"] * 1e-3), "unit": "points/s", "n_gpus": world,
+            "steps": main["steps"], "warmup": args.warmup, "ms_per_step": main["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "hermite: %d signals x N=%d at the zeros of H_N, Gaussian-windowed "
+                                   "complex noise, z = e^{-0.7i}" % (B, N),
+                       "l2": "inputs larger than L2 (64 MiB complex128 in + out + 64 MiB workspace; "
+                             "U 8 MiB stays in L2), no flush"},
+            "roofline": {"bound": "alu", "achieved": main["tflops"], "peak": FP64_NOMINAL_TFLOPS,
+                         "unit": "TFLOP/s", "frac": main["frac"], "traffic": None,
+                         "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                         "kernel": "k_herm_gemm<double> x 2 (8 N^2 flops per signal)"},
+            "phases": res,
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": 2 * main["steps"],
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -806,7 +887,7 @@ def main():
         return float(t.item())
 
     arms = {"ragged": ragged_arm, "fields2d": fields2d_arm, "backward": backward_arm,
-            "config0": config0_arm, "uniform1024": uniform1024_arm}
+            "config0": config0_arm, "uniform1024": uniform1024_arm, "hermite": hermite_arm}
     if args.workload in arms:
         arms[args.workload](args, rank, world, lct, torch, barrier, max_over_ranks, local)
         if dist is not None:

@@ -202,6 +202,33 @@ lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                         int64_t batch, lct_dtype dtype, lct_stream_t stream);
 
+/* Hermite-zero discrete fractional Fourier transform of Sec. 2, eq. (tmat):
+ *     F_z = sqrt(2 pi) U^T D(z) U,   D(z) = diag(z^0, z^1, ..., z^{N-1}),
+ * the exactly unitary (up to sqrt(2 pi), for |z| = 1) discrete transform
+ * whose eigenvectors are the discrete Hermite functions.  Its nodes x_k are
+ * the N zeros of H_N, the eigenvalues of the Jacobi matrix H (zero diagonal,
+ * off-diagonal entries sqrt(n/2), n = 1..N-1); column k of the orthogonal U
+ * is the normalised eigenvector u_k of x_k, with the signs of eq. (ortvec)
+ * (component n has the sign of H_n(x_k)).  in/out: `batch` signals of N
+ * samples at the nodes x_k (device memory, row-major [batch][N], complex
+ * dtype as lct_execute, in == out allowed); out_j is the transform at x_j.
+ * N in [2, 4096] (else LCT_ERR_N), |z| <= 1 (else LCT_ERR_ARG), batch <=
+ * 2096960.  The basis (N nodes and U, N^2 doubles plus an FP32 copy) is
+ * computed on the GPU at the first use of each N on a device -- nodes by
+ * bisection on Sturm counts, vectors by the three-term recurrence -- and
+ * cached for the life of the process; that first call synchronises.  Each
+ * call takes a workspace of batch * N + N samples from the stream-ordered
+ * allocator on `stream` and returns it there.  complex128: FP64 arithmetic;
+ * complex64: FP32 arithmetic with U rounded to FP32.  Asynchronous on
+ * `stream` after the first call for an N. */
+lct_status frft_hermite_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
+                                int64_t batch, lct_dtype dtype, lct_stream_t stream);
+/* The nodes x_k (ascending, N doubles into host memory x) and, if U is not
+ * NULL, U (N x N doubles into host memory, row-major: U[n N + k] =
+ * component n of u_k) of the Hermite-zero transform above, computed on the
+ * current device (built there if needed; synchronises). */
+lct_status frft_hermite_basis(int64_t N, double* x, double* U);
+
 /* Backward pass of lct_execute (spec differentiation; the chain rule
  * on L = S1 F S2 of Sec. 3).  grad_out: cotangent g = dl/dRe G + i dl/dIm G
  * (PyTorch's convention for a real loss l); writes grad_in = L^H g, the

@@ -69,6 +69,8 @@ def _load():
             "lct_selftest_timeout": [i32, ctypes.c_double, vp],
             "lct_set_debug": [i32],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
+            "frft_hermite_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
+            "frft_hermite_basis": [i64, dp, dp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
             "lct_plan_phase_turns": [vp, i64, up],
@@ -266,6 +268,27 @@ def frft_execute(N: int, z: complex, inp, out, batch: int, dtype: int = LCT_C64,
     z = complex(z)
     _check(_load().frft_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
                                 _stream_handle(stream)), "frft_execute")
+
+
+def frft_hermite_execute(N: int, z: complex, inp, out, batch: int, dtype: int = LCT_C64,
+                         stream=None) -> None:
+    """Hermite-zero discrete fractional transform F_z = sqrt(2 pi) U^T D(z) U
+    of signals sampled at the zeros of H_N (see include/lct.h)."""
+    z = complex(z)
+    _check(_load().frft_hermite_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
+                                        _stream_handle(stream)), "frft_hermite_execute")
+
+
+def frft_hermite_basis(N: int, with_matrix: bool = True):
+    """(nodes x [N], U [N, N] or None) of the Hermite-zero transform,
+    computed on the current GPU."""
+    x = np.empty(N, dtype=np.float64)
+    U = np.empty((N, N), dtype=np.float64) if with_matrix else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_load().frft_hermite_basis(N, x.ctypes.data_as(dp),
+                                      U.ctypes.data_as(dp) if U is not None else None),
+           "frft_hermite_basis")
+    return x, U
 
 
 def lct_output_grid(plan: int, index: int = 0, N: Optional[int] = None):

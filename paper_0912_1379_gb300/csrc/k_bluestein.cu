@@ -1,0 +1,197 @@
+// XFT for N that is not a power of two (Sec. 3: the Algorithm's DFT is "any
+// FFT").  The kernel e^{-i pi m_j m_k / (2N)} of the factorisation splits
+// exactly into two chirps and a convolution with h_n = e^{i pi n^2 / N}
+// (lct_internal.h), so one CTA per signal computes, on a shared-memory tile
+// of M = 2^L >= 2N - 1 samples:
+//   pre-chirp (samples k < N, zeros above) -> forward DFT_M -> times the
+//   kernel spectrum H/M -> inverse DFT_M -> post-chirp + scale (j < N),
+// a circular convolution of length M that equals the linear one for j < N
+// (Bluestein's algorithm).  Each sample is read from HBM once and written
+// once; the spectrum table (M complex values per N) is shared by every
+// signal of that N and stays in L2.  Both DFTs are the Stockham engine of
+// xft_engine.cuh.  Sizes: N <= 8192 (complex64, M <= 16384), N <= 4096
+// (complex128, M <= 8192).
+#include "xft_engine.cuh"
+#include "xft_chirp.cuh"
+
+namespace {
+
+using namespace xft;
+
+template <int L>
+struct blue_shape {
+    static constexpr int T = shape<L>::T;
+    static constexpr int SPC = T >= 256 ? 1 : 256 / T;     // signals per CTA
+    static constexpr int THREADS = T * SPC;
+};
+
+template <int L, class R>
+constexpr int blue_min_blocks() {
+    constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
+    constexpr int b = per_sm / blue_shape<L>::THREADS;
+    return b > 0 ? b : 1;
+}
+
+// e^{2 pi i [phi m^2 + off]} with m = 2k - n + 1 (|m| < 2^16), phi the
+// descriptor's turn fraction (64 bits for FP32, 128 for FP64).
+template <class R>
+__device__ __forceinline__ cpx<R> chirp_any(uint64_t phi_hi, uint64_t phi_lo, uint64_t off, int k,
+                                            int n) {
+    const uint32_t m2 = m_squared(k, n);
+    if constexpr (sizeof(R) == 4)
+        return expi_turn32<true>(phase32(phi_hi, m2) + (uint32_t)((off + 0x80000000ull) >> 32));
+    else
+        return expi_turn64(phase64(phi_hi, phi_lo, m2) + off);
+}
+
+template <class R>
+__device__ __forceinline__ cpx<R> ld_spec(const cpx<R>* p) {
+    return ld_tw<R>(p);
+}
+
+template <int L, class R>
+__global__ void __launch_bounds__(blue_shape<L>::THREADS, (blue_min_blocks<L, R>()))
+k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+           const lct_desc* __restrict__ desc, int desc_step, int64_t count, int n,
+           const cpx<R>* __restrict__ tw, const cpx<R>* __restrict__ spec,
+           const int32_t* __restrict__ idx, int32_t* __restrict__ status) {
+    using S = shape<L>;
+    using F = blue_shape<L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int sl = tid / S::T;
+    const int i = tid - sl * S::T;
+    const int64_t sig = (int64_t)blockIdx.x * F::SPC + sl;
+    bool active = sig < count;
+    const int64_t gsig = idx ? (active ? idx[sig] : 0) : sig;
+    const lct_desc D = desc[desc_step && active ? gsig : 0];
+    if (active && (D.kind != LCT_KIND_BLUE || D.n != n || D.log2n != L || D.offset < 0)) {
+        if (i == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+        active = false;
+    }
+    const int64_t base = desc_step ? D.offset : sig * (int64_t)n;
+    buf += sl * S::NP;
+    const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+
+    cpx<R> v[S::E];
+    // load samples k < N with the pre-chirp; the rest of the tile is zero
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const int k = i + e * S::T;
+        cpx<R> f = {R(0), R(0)};
+        if (active && k < n) {
+            f = ld_stream(in + base + k);
+            cpx<R> w = chirp_any<R>(D.in_hi, D.in_lo, 0, k, n);
+            if (decay) {
+                const uint32_t m2 = m_squared(k, n);
+                if constexpr (sizeof(R) == 4) w = cscale(w, expf(-(float)D.decay * (float)m2));
+                else w = cscale(w, exp(-D.decay * (double)m2));
+            }
+            f = cmul(f, w);
+        }
+        v[e] = f;
+    }
+    dft_signal<L, -1>(v, buf, i, tw);
+    // circular convolution with h: times its spectrum (already divided by M)
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) v[e] = cmul(v[e], ld_spec<R>(spec + i + e * S::T));
+    __syncthreads();                  // the forward DFT's last exchange is fully read
+    dft_signal<L, +1>(v, buf, i, tw);
+    if (active) {
+        const R sc = (R)D.scale;
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int j = i + e * S::T;
+            if (j < n) out[base + j] = cscale(cmul(v[e], chirp_any<R>(D.out_hi, D.out_lo, D.out_c, j, n)), sc);
+        }
+    }
+}
+
+template <int L, class R>
+cudaError_t launch_blue_l(int n, const void* in, void* out, const lct_desc* desc, int desc_step,
+                          int64_t count, const void* tw, const void* spec, const int32_t* idx,
+                          int32_t* status, cudaStream_t stream) {
+    using S = shape<L>;
+    using F = blue_shape<L>;
+    const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
+    auto kern = k_xft_blue<L, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (count + F::SPC - 1) / F::SPC;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)blocks, F::THREADS, smem, stream>>>(
+        (const cpx<R>*)in, (cpx<R>*)out, desc, desc_step, count, n, (const cpx<R>*)tw,
+        (const cpx<R>*)spec, idx, status);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t blue_dispatch(int n, const void* in, void* out, const lct_desc* desc, int desc_step,
+                          int64_t count, const void* tw, const void* spec, const int32_t* idx,
+                          int32_t* status, cudaStream_t stream) {
+    switch (lct_blue_log2m(n)) {
+#define LCT_CASE(L) \
+    case L: return launch_blue_l<L, R>(n, in, out, desc, desc_step, count, tw, spec, idx, status, stream);
+        LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8)
+        LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12) LCT_CASE(13)
+#undef LCT_CASE
+        case 14:
+            if constexpr (sizeof(R) == 4)
+                return launch_blue_l<14, R>(n, in, out, desc, desc_step, count, tw, spec, idx, status,
+                                            stream);
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// b == 0 for N that is not a power of two: G_j = scale e^{2 pi i [phi_out m_j^2 + c_out]} f_j,
+// one CTA per signal (grid-stride over signals), threads over samples.
+template <class R>
+__global__ void k_diag_any(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
+                           const lct_desc* __restrict__ desc, int desc_step, int64_t count, int n,
+                           const int32_t* __restrict__ idx, int32_t* __restrict__ status) {
+    for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
+        const lct_desc& D = desc[desc_step ? (idx ? idx[s] : s) : 0];
+        if (D.kind != LCT_KIND_DIAGN || D.n != n || D.offset < 0) {
+            if (threadIdx.x == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
+            continue;
+        }
+        const int64_t base = desc_step ? D.offset : s * (int64_t)n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const cpx<R> w = chirp_any<R>(D.out_hi, D.out_lo, D.out_c, j, n);
+            out[base + j] = cscale(cmul(in[base + j], w), (R)D.scale);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t lct_launch_blue(int dtype, int64_t n, const void* in, void* out, const lct_desc* desc,
+                            int desc_step, int64_t count, const void* tw, const void* spec,
+                            const int32_t* idx, int32_t* status, cudaStream_t stream) {
+    if (!lct_blue_supported(dtype, n) || !spec) return cudaErrorInvalidValue;
+    if (dtype == 0)
+        return blue_dispatch<float>((int)n, in, out, desc, desc_step, count, tw, spec, idx, status,
+                                    stream);
+    return blue_dispatch<double>((int)n, in, out, desc, desc_step, count, tw, spec, idx, status,
+                                 stream);
+}
+
+cudaError_t lct_launch_diag_any(int dtype, int64_t n, const void* in, void* out,
+                                const lct_desc* desc, int desc_step, int64_t count,
+                                const int32_t* idx, int32_t* status, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(count < 152 * 16 ? count : 152 * 16);
+    const int th = n >= 256 ? 256 : 64;
+    if (dtype == 0)
+        k_diag_any<float><<<grid, th, 0, stream>>>((const cpx<float>*)in, (cpx<float>*)out, desc,
+                                                   desc_step, count, (int)n, idx, status);
+    else
+        k_diag_any<double><<<grid, th, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out, desc,
+                                                    desc_step, count, (int)n, idx, status);
+    return cudaGetLastError();
+}

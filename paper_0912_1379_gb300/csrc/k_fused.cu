@@ -15,9 +15,11 @@ using namespace xft;
 // ONE = false: several signals per CTA for small N (256 threads);
 // ONE = true: one signal per CTA, for batches too small to give every SM a
 // CTA of packed signals (latency: FP64 work spread over more SMs).
-template <int L, bool ONE = false>
+// LE: log2 of the samples per thread (4: radix-16 passes; 2: radix-4 passes
+// with four times the threads per signal, for latency).
+template <int L, bool ONE = false, int LE = 4>
 struct fused_shape {
-    static constexpr int T = shape<L>::T;
+    static constexpr int T = shape<L, LE>::T;
     static constexpr int SPC = (T >= 256 || ONE) ? 1 : 256 / T;     // signals per CTA
     static constexpr int THREADS = T * SPC;
 };
@@ -25,22 +27,22 @@ struct fused_shape {
 // Minimum resident CTAs per SM for __launch_bounds__: keeps FP32 kernels at
 // <= 64 registers (1024 resident threads fill the 64K register file) and
 // FP64 kernels at <= 128 (512 resident threads).
-template <int L, class R, bool ONE = false>
+template <int L, class R, bool ONE = false, int LE = 4>
 constexpr int min_blocks() {
     constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
-    constexpr int th = fused_shape<L, ONE>::THREADS;
+    constexpr int th = fused_shape<L, ONE, LE>::THREADS;
     constexpr int b = per_sm / th > 0 ? per_sm / th : 1;
     return b > 32 ? 32 : b;
 }
 
-template <int L, class R, bool ONE>
-__global__ void __launch_bounds__(fused_shape<L, ONE>::THREADS, (min_blocks<L, R, ONE>()))
+template <int L, class R, bool ONE, int LE>
+__global__ void __launch_bounds__(fused_shape<L, ONE, LE>::THREADS, (min_blocks<L, R, ONE, LE>()))
 k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
             const lct_desc* __restrict__ desc, int desc_step, int64_t count,
             const cpx<R>* __restrict__ tw, const int32_t* __restrict__ idx,
             int32_t* __restrict__ status) {
-    using S = shape<L>;
-    using F = fused_shape<L, ONE>;
+    using S = shape<L, LE>;
+    using F = fused_shape<L, ONE, LE>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<R>* smem = reinterpret_cast<cpx<R>*>(smem_raw);
     const int tid = threadIdx.x;
@@ -69,7 +71,7 @@ k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
         if (active) f = ld_stream(in + base + n);
         v[e] = cmul(f, pre_w<L, R>(D, n, decay));
     }
-    dft_signal<L, -1>(v, buf, i, tw);
+    dft_signal<L, -1, false, LE>(v, buf, i, tw);
     // global store (sample i + e T) with the post-chirp and scale
     if (active) {
         const R sc = (R)D.scale;
@@ -206,14 +208,14 @@ cudaError_t launch_tma(const void* in, void* out, const lct_desc* desc, int desc
     return cudaGetLastError();
 }
 
-template <int L, class R, bool ONE>
+template <int L, class R, bool ONE, int LE = 4>
 cudaError_t launch_shape(const void* in, void* out, const lct_desc* desc, int desc_step,
                          int64_t count, const void* tw, const int32_t* idx, int32_t* status,
                          cudaStream_t stream) {
-    using S = shape<L>;
-    using F = fused_shape<L, ONE>;
+    using S = shape<L, LE>;
+    using F = fused_shape<L, ONE, LE>;
     const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
-    auto kern = k_xft_fused<L, R, ONE>;
+    auto kern = k_xft_fused<L, R, ONE, LE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -241,16 +243,28 @@ int sm_count() {
 
 // Packed signals per CTA, unless that leaves SMs idle: then one signal per
 // CTA, so that a small batch (the 12-signal FP64 case, say) runs on as many
-// SMs as it has signals.
+// SMs as it has signals.  FP64 signals then also take four samples per
+// thread (radix-4 passes, four times the threads), which shortens each
+// thread's chain of FP64 phase and butterfly arithmetic (uniform plans; the
+// radix-4 twiddle table is created here, outside any graph capture).
 template <int L, class R>
 cudaError_t launch_one(const void* in, void* out, const lct_desc* desc, int desc_step,
                        int64_t count, const void* tw, const int32_t* idx, int32_t* status,
                        cudaStream_t stream) {
     if constexpr (fused_shape<L>::SPC > 1) {
         const int64_t packed = (count + fused_shape<L>::SPC - 1) / fused_shape<L>::SPC;
-        if (packed < sm_count())
+        if (packed < sm_count()) {
+            if constexpr (sizeof(R) == 8 && L >= 5) {
+                if (!idx) {
+                    const void* tw4 = lct_twiddle_table_le(1, L, 2);
+                    if (!tw4) return cudaErrorMemoryAllocation;
+                    return launch_shape<L, R, true, 2>(in, out, desc, desc_step, count, tw4, idx,
+                                                       status, stream);
+                }
+            }
             return launch_shape<L, R, true>(in, out, desc, desc_step, count, tw, idx, status,
                                             stream);
+        }
     }
     return launch_shape<L, R, false>(in, out, desc, desc_step, count, tw, idx, status, stream);
 }

@@ -83,12 +83,12 @@ __global__ void k_diag_chunks(const cpx<R>* __restrict__ in, cpx<R>* __restrict_
 // Debug scan for NaN / infinite samples, one CTA per signal (grid-stride).
 template <class R>
 __global__ void k_scan(const cpx<R>* __restrict__ out, const lct_desc* __restrict__ desc,
-                       int desc_step, int64_t count, int log2n, int32_t* __restrict__ status) {
+                       int desc_step, int64_t count, int64_t len, int32_t* __restrict__ status) {
     for (int64_t s = blockIdx.x; s < count; s += gridDim.x) {
-        const int L = desc_step ? desc[s].log2n : log2n;
-        const int64_t base = desc_step ? desc[s].offset : s << log2n;
+        const int64_t nn = desc_step ? desc[s].n : len;
+        const int64_t base = desc_step ? desc[s].offset : s * len;
         bool bad = false;
-        for (int n = threadIdx.x; n < (1 << L); n += blockDim.x) {
+        for (int64_t n = threadIdx.x; n < nn; n += blockDim.x) {
             const cpx<R> v = out[base + n];
             bad |= !isfinite(v.x) || !isfinite(v.y);
         }
@@ -223,15 +223,15 @@ cudaError_t lct_launch_diag_chunks(int dtype, const void* in, void* out, const l
 }
 
 cudaError_t lct_launch_scan(int dtype, const void* out, const lct_desc* desc, int desc_step,
-                            int64_t count, int log2n, int32_t* status, cudaStream_t stream) {
+                            int64_t count, int64_t len, int32_t* status, cudaStream_t stream) {
     if (count <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(count < 4096 ? count : 4096);
     if (dtype == 0)
         k_scan<float><<<grid, 256, 0, stream>>>((const cpx<float>*)out, desc, desc_step, count,
-                                                log2n, status);
+                                                len, status);
     else
         k_scan<double><<<grid, 256, 0, stream>>>((const cpx<double>*)out, desc, desc_step, count,
-                                                 log2n, status);
+                                                 len, status);
     return cudaGetLastError();
 }
 

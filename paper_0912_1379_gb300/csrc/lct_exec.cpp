@@ -183,10 +183,26 @@ int group_variant(lct_dtype dtype, int log2n) {
     return default_variant(dtype, log2n);
 }
 
+// N that is not a power of two: the chirp-convolution kernel (b != 0) or the
+// diagonal (b == 0) for `count` signals of one N.
+lct_status run_blue(lct_plan p, int kind, int64_t n, const void* in, void* out, int64_t count,
+                    int desc_step, const int32_t* idx, cudaStream_t stream) {
+    if (kind == LCT_KIND_DIAGN)
+        return from_cuda(lct_launch_diag_any(p->dtype, n, in, out, p->d_desc, desc_step, count, idx,
+                                             p->d_status, stream));
+    const int lm = lct_blue_log2m(n);
+    const void* tw = lct_twiddle_table(p->dtype, lm);
+    const void* spec = lct_blue_spectrum(p->dtype, n);
+    if ((lm >= 5 && !tw) || !spec) return LCT_ERR_OOM;
+    return from_cuda(lct_launch_blue(p->dtype, n, in, out, p->d_desc, desc_step, count, tw, spec,
+                                     idx, p->d_status, stream));
+}
+
 // Launch one group of a ragged plan on `stream`.
 lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, void* out,
                         cudaStream_t stream) {
     const int32_t* idx = p->d_idx + g.idx_off;
+    if (blue_kind(g.kind)) return run_blue(p, g.kind, g.n, in, out, g.count, 1, idx, stream);
     if (g.kind == LCT_KIND_DIAG)
         return from_cuda(lct_launch_diag_chunks(p->dtype, in, out, p->d_desc, idx,
                                                 p->d_chunks + 4 * g.chunk_off, g.nchunks,
@@ -216,7 +232,7 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
     size_t tp_need = 0;
     for (auto& g : p->groups) {
         g.tp_off = -1;
-        if (g.kind == LCT_KIND_DIAG || !lct_twopass_supported(p->dtype, g.log2n)) continue;
+        if (g.kind != LCT_KIND_XFT || !lct_twopass_supported(p->dtype, g.log2n)) continue;
         if (group_variant(p->dtype, g.log2n) != 7) continue;
         int l1, l2;
         lct_twopass_split(g.log2n, &l1, &l2);
@@ -232,7 +248,13 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
         if (st != LCT_OK) return st;
     }
     for (const auto& g : p->groups) {
-        if (g.kind == LCT_KIND_DIAG) continue;
+        if (g.kind == LCT_KIND_DIAG || g.kind == LCT_KIND_DIAGN) continue;
+        if (g.kind == LCT_KIND_BLUE) {
+            if ((g.log2n >= 5 && !lct_twiddle_table(p->dtype, g.log2n)) ||
+                !lct_blue_spectrum(p->dtype, g.n))
+                return LCT_ERR_OOM;
+            continue;
+        }
         const int lm = lct_cluster_local_log2(p->dtype, g.log2n);
         if (lm >= 0 && !lct_twiddle_table(p->dtype, lm)) return LCT_ERR_OOM;
         if (g.log2n >= 5 && lct_fused_supported(p->dtype, g.log2n) &&
@@ -310,6 +332,10 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
     const int desc_step = plan->is_batch ? 1 : 0;
     const lct_desc& D0 = plan->desc[0];
     const int log2n = D0.log2n;
+    if (blue_kind(D0.kind)) {
+        if (plan->prec != LCT_PREC_NATIVE) return LCT_ERR_UNSUPPORTED;
+        return run_blue(plan, D0.kind, D0.n, in, out, batch, desc_step, nullptr, stream);
+    }
     if (D0.kind == LCT_KIND_DIAG)
         return from_cuda(lct_launch_diag(plan->dtype, log2n, in, out, plan->d_desc, desc_step,
                                          batch, nullptr, plan->d_status, stream));
@@ -334,8 +360,7 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
 // device status word.
 lct_status debug_check(lct_plan plan, const void* out, int64_t count, cudaStream_t stream) {
     const int desc_step = plan->is_batch ? 1 : 0;
-    const int log2n = plan->desc[0].log2n;
-    if (lct_launch_scan(plan->dtype, out, plan->d_desc, desc_step, count, log2n, plan->d_status,
+    if (lct_launch_scan(plan->dtype, out, plan->d_desc, desc_step, count, plan->desc[0].n, plan->d_status,
                         stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
         return LCT_ERR_CUDA;
@@ -540,8 +565,8 @@ lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, voi
     cplx z(z_re, z_im);
     double az = std::abs(z);
     if (!std::isfinite(az) || az == 0.0 || az > 1.0 + 1e-15) return LCT_ERR_ARG;
-    if (ilog2_exact(N) < 0) return LCT_ERR_N;
     if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
+    if (ilog2_exact(N) < 0 && !lct_blue_supported(dtype, N)) return LCT_ERR_N;
     double p[8];
     double frft_scale_abs;
     double frft_scale_turns;

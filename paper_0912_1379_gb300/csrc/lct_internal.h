@@ -19,11 +19,21 @@
 //
 // kind == LCT_KIND_DIAG (b == 0): G_j = scale e^{2 pi i [phi_out m_j^2 + c_out]} f_j
 // with phi_out = Re(c/d) pi / (32 N) (the phase c x_j^2/(2d)), scale e^{2 pi i c_out} = sqrt(d).
+//
+// N not a power of two.  The DFT kernel of the factorisation is a chirp
+// convolution: with m_j - m_k = 2 (j - k),
+//   e^{-i pi m_j m_k / (2N)} = e^{-i pi m_j^2/(4N)} e^{-i pi m_k^2/(4N)} e^{i pi (j-k)^2 / N},
+// so  G_j = scale e^{2 pi i [phi_out' m_j^2 + c_out]} sum_k h_{j-k} e^{2 pi i phi_in' m_k^2} f_k
+// with h_n = e^{i pi n^2 / N}, phi_in' = phi_in - 1/(8N), phi_out' = phi_out - 1/(8N) and
+// scale e^{2 pi i c_out} = dx / sqrt(2 pi i b) (no centring phases).  The
+// convolution runs as a circular one of length M = 2^log2n >= 2N - 1
+// (Bluestein's algorithm): kind LCT_KIND_BLUE, n = N.  b == 0 signals of such
+// N are kind LCT_KIND_DIAGN (the diagonal above, log2n unused).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
 
-enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1 };
+enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1, LCT_KIND_BLUE = 2, LCT_KIND_DIAGN = 3 };
 enum { LCT_FLAG_DECAY = 1 };
 
 struct __align__(16) lct_desc {
@@ -33,10 +43,10 @@ struct __align__(16) lct_desc {
     int64_t offset;           // element offset of the signal in in/out
     double scale;             // |prefactor|
     double decay;             // Im(beta_in) (pre-chirp magnitude e^{-decay m^2})
-    int32_t log2n;
+    int32_t log2n;            // log2 N; for LCT_KIND_BLUE log2 M (M >= 2N - 1)
     int32_t kind;
     int32_t flags;
-    int32_t pad;
+    int32_t n;                // N (every kind)
 };
 static_assert(sizeof(lct_desc) == 80, "descriptor layout");
 
@@ -61,6 +71,9 @@ const void* lct_twiddle_table_r8(int log2n);
 // 2^le passes, le = 4 or 3): every entry (wx, wy) stored as
 // {(wx, wx), (wy, wy)} (16 bytes).
 const void* lct_twiddle_table_pair(int log2n, int le = 4);
+// Table of the engine with radix 2^le passes (le = 2, 3 or 4) in the dtype's
+// precision, same layout.
+const void* lct_twiddle_table_le(int dtype, int log2n, int le);
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 // Fused chirp-DFT-chirp on N = 2^log2n, one or several signals per CTA.
@@ -192,10 +205,32 @@ size_t lct_grad_finalize_scratch_bytes();
 
 // Debug scan: records LCT_DEV_NONFINITE in *status if any sample of the
 // `count` output signals is NaN or infinite.  desc_step = 0: signal s is
-// elements [s N, (s + 1) N) with N = 2^log2n; desc_step = 1: desc[s].offset
-// and desc[s].log2n.
+// elements [s n, (s + 1) n); desc_step = 1: desc[s].offset and desc[s].n.
 cudaError_t lct_launch_scan(int dtype, const void* out, const lct_desc* desc, int desc_step,
-                            int64_t count, int log2n, int32_t* status, cudaStream_t stream);
+                            int64_t count, int64_t n, int32_t* status, cudaStream_t stream);
+
+// ---- N not a power of two (k_bluestein.cu, lct_phase.cpp) ------------------
+// Largest such N per dtype (the convolution of length M <= 16384 complex64 /
+// 8192 complex128 fits one CTA's shared memory).
+constexpr int64_t kBlueMaxN64 = 8192, kBlueMaxN128 = 4096;
+// log2 M, M the smallest power of two >= 2N - 1.
+int lct_blue_log2m(int64_t n);
+bool lct_blue_supported(int dtype, int64_t n);
+// Host: device table of the kernel spectrum H_j / M, j < M, H = DFT_M of the
+// circularly placed chirp h_n = e^{i pi n^2/N} (|n| < N), for this N on the
+// current device, in the dtype's precision (cached for the process).
+const void* lct_blue_spectrum(int dtype, int64_t n);
+// Chirp - FFT_M - spectrum - inverse FFT_M - chirp for `count` signals of one
+// N (kind LCT_KIND_BLUE), one CTA per signal or group of signals.  tw:
+// lct_twiddle_table(dtype, log2 M); spec: lct_blue_spectrum(dtype, n).
+// idx as for lct_launch_fused (descriptors of another N or kind are flagged).
+cudaError_t lct_launch_blue(int dtype, int64_t n, const void* in, void* out, const lct_desc* desc,
+                            int desc_step, int64_t count, const void* tw, const void* spec,
+                            const int32_t* idx, int32_t* status, cudaStream_t stream);
+// b == 0 signals of one N that is not a power of two (kind LCT_KIND_DIAGN).
+cudaError_t lct_launch_diag_any(int dtype, int64_t n, const void* in, void* out,
+                                const lct_desc* desc, int desc_step, int64_t count,
+                                const int32_t* idx, int32_t* status, cudaStream_t stream);
 
 // Plain FP64 baseline pieces.  work: complex128 [count][N].
 cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* work,

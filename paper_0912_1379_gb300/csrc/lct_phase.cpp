@@ -134,22 +134,29 @@ bool symplectic(cplx a, cplx b, cplx c, cplx d) {
 }  // namespace
 
 // Build the descriptor of one signal.  Returns LCT_OK or a validation error.
+// N = 2 .. 65536; N that is not a power of two gets the chirp-convolution
+// form (kinds LCT_KIND_BLUE / LCT_KIND_DIAGN, see lct_internal.h); which
+// such N a dtype supports is checked by the plan.
 lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
-    int log2n = ilog2_exact(N);
-    if (log2n < 0) return LCT_ERR_N;
+    if (N < 2 || N > 65536) return LCT_ERR_N;
+    const int log2n = ilog2_exact(N);
+    const bool pow2 = log2n >= 0;
     for (int i = 0; i < 8; ++i)
         if (!std::isfinite(p[i])) return LCT_ERR_ARG;
     cplx a(p[0], p[1]), b(p[2], p[3]), c(p[4], p[5]), d(p[6], p[7]);
     if (!symplectic(a, b, c, d)) return LCT_ERR_NOT_SYMPLECTIC;
     std::memset(D, 0, sizeof(*D));
     D->offset = offset;
-    D->log2n = log2n;
+    D->log2n = pow2 ? log2n : 0;
+    D->n = (int32_t)N;
+    const dd DN = {(double)N, 0.0};
     uint64_t hi, lo;
     if (b == cplx(0.0, 0.0)) {
         // b = 0: G_j = sqrt(d) e^{i c x_j^2 / (2d)} f_j on y_j = x_j / d;
         // c x^2/(2d) = Re(c/d) pi^2 m^2/(16N) -> turns Re(c/d) pi / (32N).
-        D->kind = LCT_KIND_DIAG;
-        dd t = dd_ldexp(dd_mul(dd_re_div(c, d), DD_PI), -(5 + log2n));
+        D->kind = pow2 ? LCT_KIND_DIAG : LCT_KIND_DIAGN;
+        dd t = pow2 ? dd_ldexp(dd_mul(dd_re_div(c, d), DD_PI), -(5 + log2n))
+                    : dd_div(dd_ldexp(dd_mul(dd_re_div(c, d), DD_PI), -5), DN);
         dd_to_turns128(t, &hi, &lo);
         D->out_hi = hi;
         D->out_lo = lo;
@@ -158,16 +165,38 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
         D->out_c = double_to_turns64(std::arg(sd) / (2.0 * M_PI));
         return LCT_OK;
     }
+    cplx ab = a / b;
+    double decay = ab.imag() * M_PI * M_PI / (16.0 * (double)N);
+    D->decay = decay;
+    if (decay != 0.0) D->flags |= LCT_FLAG_DECAY;
+    double dx = M_PI / std::sqrt(2.0 * (double)N);
+    cplx pre = dx / std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
+    D->scale = std::abs(pre);
+    if (!pow2) {
+        // chirp-convolution form: phi_in - 1/(8N), phi_out - 1/(8N), constant
+        // arg(dx / sqrt(2 pi i b)) only
+        D->kind = LCT_KIND_BLUE;
+        D->log2n = lct_blue_log2m(N);
+        const dd one = {1.0, 0.0};
+        dd tin = dd_div(dd_sub(dd_ldexp(dd_mul(dd_re_div(a, b), DD_PI), -2), one),
+                        dd_ldexp(DN, 3));                     // (Re(a/b) pi/4 - 1) / (8N)
+        dd_to_turns128(tin, &hi, &lo);
+        D->in_hi = hi;
+        D->in_lo = lo;
+        dd tout = dd_div(dd_sub(dd_div(dd_re_mul(b, d), dd_ldexp(DD_PI, 1)), {0.125, 0.0}),
+                         DN);                                 // (Re(bd)/(2 pi) - 1/8) / N
+        dd_to_turns128(tout, &hi, &lo);
+        D->out_hi = hi;
+        D->out_lo = lo;
+        D->out_c = double_to_turns64(std::arg(pre) / (2.0 * M_PI));
+        return LCT_OK;
+    }
     D->kind = LCT_KIND_XFT;
     // pre-chirp a x_k^2/(2b) = (a/b) pi^2 m^2 / (16 N): turns (a/b) pi / (32 N)
     dd tin = dd_ldexp(dd_mul(dd_re_div(a, b), DD_PI), -(5 + log2n));
     dd_to_turns128(tin, &hi, &lo);
     D->in_hi = hi;
     D->in_lo = lo;
-    cplx ab = a / b;
-    double decay = ab.imag() * M_PI * M_PI / (16.0 * (double)N);
-    D->decay = decay;
-    if (decay != 0.0) D->flags |= LCT_FLAG_DECAY;
     // post-chirp d y_j^2/(2b) = b d m^2 / N: turns Re(b d) / (2 pi N)
     dd tout = dd_ldexp(dd_div(dd_re_mul(b, d), DD_PI), -(1 + log2n));
     dd_to_turns128(tout, &hi, &lo);
@@ -176,9 +205,6 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
     // constant: -(N-1)^2/(4N) turns (exact) + arg(dx / sqrt(2 pi i b)) / (2 pi)
     uint64_t r = (uint64_t)(((N - 1) * (N - 1)) % (4 * N));
     uint64_t centre = (uint64_t)0 - (r << (62 - log2n));       // -r / (4N) as Q0.64
-    double dx = M_PI / std::sqrt(2.0 * (double)N);
-    cplx pre = dx / std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
-    D->scale = std::abs(pre);
     D->out_c = centre + double_to_turns64(std::arg(pre) / (2.0 * M_PI));
     return LCT_OK;
 }
@@ -243,6 +269,17 @@ const void* lct_twiddle_table(int dtype, int log2n) {
     return cached_table(key, [&] { return build_twiddles<double>(log2n); });
 }
 
+const void* lct_twiddle_table_le(int dtype, int log2n, int le) {
+    if (le < 2 || le > 4 || log2n <= le) return nullptr;
+    if (le == 4) return lct_twiddle_table(dtype, log2n);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    const auto key = std::make_tuple(dev, 40 + 2 * le + dtype, log2n);
+    if (dtype == LCT_C64) return cached_table(key, [&] { return build_twiddles<float>(log2n, le); });
+    return cached_table(key, [&] { return build_twiddles<double>(log2n, le); });
+}
+
 const void* lct_twiddle_table_r8(int log2n) {
     if (log2n < 4) return nullptr;
     int dev = -1;
@@ -267,6 +304,82 @@ const void* lct_twiddle_table_pair(int log2n, int le) {
         }
         return b;
     });
+}
+
+// ---------------------------------------------------------------------------
+// chirp-convolution (Bluestein) spectra for N that is not a power of two
+// ---------------------------------------------------------------------------
+int lct_blue_log2m(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < 2 * n - 1) ++l;
+    return l;
+}
+
+bool lct_blue_supported(int dtype, int64_t n) {
+    return n >= 3 && n <= (dtype == LCT_C64 ? kBlueMaxN64 : kBlueMaxN128) && ilog2_exact(n) < 0;
+}
+
+namespace {
+// In-place forward DFT (sign -1) of a power-of-two length: iterative radix-2
+// with the twiddles e^{-2 pi i k / M} taken in long double.
+void host_fft(std::vector<std::complex<double>>& a) {
+    const size_t M = a.size();
+    for (size_t i = 1, j = 0; i < M; ++i) {
+        size_t bit = M >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    std::vector<std::complex<double>> w(M / 2);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (size_t k = 0; k < M / 2; ++k) {
+        const long double ang = -two_pi * (long double)k / (long double)M;
+        w[k] = {(double)cosl(ang), (double)sinl(ang)};
+    }
+    for (size_t len = 2; len <= M; len <<= 1) {
+        const size_t step = M / len;
+        for (size_t i = 0; i < M; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w[k * step];
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// H_j / M for the chirp h_n = e^{i pi n^2 / N}, |n| < N, placed circularly
+// (h[n] for n >= 0, h[M - n] for n < 0) in length M; the phase n^2/(2N)
+// turns is reduced exactly in integers.
+template <class T>
+std::vector<T> build_blue_spectrum(int64_t n) {
+    const int64_t M = (int64_t)1 << lct_blue_log2m(n);
+    std::vector<std::complex<double>> h((size_t)M, {0.0, 0.0});
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t r = (t * t) % (2 * n);
+        const long double ang = two_pi * (long double)r / (long double)(2 * n);
+        const std::complex<double> v = {(double)cosl(ang), (double)sinl(ang)};
+        h[(size_t)t] = v;
+        if (t > 0) h[(size_t)(M - t)] = v;
+    }
+    host_fft(h);
+    std::vector<T> out(2 * (size_t)M);
+    for (int64_t j = 0; j < M; ++j) {
+        out[2 * j] = (T)(h[(size_t)j].real() / (double)M);
+        out[2 * j + 1] = (T)(h[(size_t)j].imag() / (double)M);
+    }
+    return out;
+}
+}  // namespace
+
+const void* lct_blue_spectrum(int dtype, int64_t n) {
+    if (!lct_blue_supported(dtype, n)) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    const auto key = std::make_tuple(dev, 100 + dtype, (int)n);
+    if (dtype == LCT_C64) return cached_table(key, [&] { return build_blue_spectrum<float>(n); });
+    return cached_table(key, [&] { return build_blue_spectrum<double>(n); });
 }
 
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {

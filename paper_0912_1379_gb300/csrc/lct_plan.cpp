@@ -18,6 +18,7 @@
 #include <numeric>
 #include <queue>
 #include <string>
+#include <tuple>
 #include <vector>
 
 // ---------------------------------------------------------------------------
@@ -243,6 +244,9 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
     p->N0 = N[0];
     for (int64_t s = 0; s < count; ++s) {
         if (offsets && offsets[s] < 0) { delete p; return LCT_ERR_ARG; }
+        // N: a power of two in [2, 65536], or another N the chirp-convolution
+        // kernel takes in this dtype
+        if (ilog2_exact(N[s]) < 0 && !lct_blue_supported(dtype, N[s])) { delete p; return LCT_ERR_N; }
         lct_status st = make_desc(N[s], abcd + 8 * s, offsets ? offsets[s] : 0, &p->desc[s]);
         if (st != LCT_OK) { delete p; return st; }
         if (N[s] != p->N0) p->N0 = 0;
@@ -253,12 +257,13 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
     for (int64_t s = 1; s < count; ++s)
         if (p->desc[s].kind != p->desc[0].kind) mixed_kind = true;
     if (is_batch && (p->N0 == 0 || mixed_kind)) {
-        // Group by (N, kind), largest N first.
+        // Group by (N, kind), largest N first (tile size log2n, then N).
         p->ragged = true;
-        std::map<std::pair<int, int>, std::vector<int32_t>, std::greater<std::pair<int, int>>> by;
+        typedef std::tuple<int, int, int> gkey;                   // (log2n, n, kind)
+        std::map<gkey, std::vector<int32_t>, std::greater<gkey>> by;
         for (int64_t s = 0; s < count; ++s) {
             const lct_desc& D = p->desc[s];
-            by[{D.log2n, D.kind}].push_back((int32_t)s);
+            by[gkey{D.log2n, D.n, D.kind}].push_back((int32_t)s);
         }
         lct_plan_s::group diag;
         diag.log2n = -1;
@@ -266,9 +271,9 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
         diag.count = 0;
         std::vector<int32_t> diag_idx;
         for (auto& kv : by) {
-            if (kv.first.second == LCT_KIND_DIAG) {
+            if (std::get<2>(kv.first) == LCT_KIND_DIAG) {
                 // chunks of kDiagChunk elements, or whole small signals packed
-                const int L = kv.first.first;
+                const int L = std::get<0>(kv.first);
                 const int64_t n = (int64_t)1 << L;
                 const int64_t pos0 = (int64_t)diag_idx.size();
                 const int64_t m = (int64_t)kv.second.size();
@@ -288,8 +293,9 @@ lct_status new_plan(lct_plan* out, lct_dtype dtype, int64_t count, const int64_t
                 continue;
             }
             lct_plan_s::group g;
-            g.log2n = kv.first.first;
-            g.kind = kv.first.second;
+            g.log2n = std::get<0>(kv.first);
+            g.n = std::get<1>(kv.first);
+            g.kind = std::get<2>(kv.first);
             g.count = (int64_t)kv.second.size();
             g.idx_off = (int64_t)p->idx.size();
             p->idx.insert(p->idx.end(), kv.second.begin(), kv.second.end());
@@ -343,10 +349,17 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
     if (!plan) return LCT_ERR_ARG;
     switch (precision) {
         case LCT_PREC_NATIVE:
+            plan->prec = precision;
+            return LCT_OK;
         case LCT_PREC_PLAIN64:
+            // the unfused paths take powers of two only
+            if (plan->desc[0].kind == LCT_KIND_BLUE || plan->desc[0].kind == LCT_KIND_DIAGN)
+                return LCT_ERR_UNSUPPORTED;
             plan->prec = precision;
             return LCT_OK;
         case LCT_PREC_PLAIN32:
+            if (plan->desc[0].kind == LCT_KIND_BLUE || plan->desc[0].kind == LCT_KIND_DIAGN)
+                return LCT_ERR_UNSUPPORTED;
             // FP32 chirps around cuFFT C2C: complex64 plans of one N
             if (plan->dtype != LCT_C64 || plan->ragged || plan->N0 == 0) return LCT_ERR_UNSUPPORTED;
             plan->prec = precision;
@@ -358,6 +371,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
             // no DFT and run their diagonal kernel whatever the precision)
             if (plan->dtype != LCT_C64 || plan->ragged || plan->N0 == 0) return LCT_ERR_UNSUPPORTED;
             const int log2n = ilog2_exact(plan->N0);
+            if (log2n < 0) return LCT_ERR_UNSUPPORTED;
             if (plan->desc[0].kind == LCT_KIND_XFT && !lct_split_supported(plan->dtype, log2n))
                 return LCT_ERR_UNSUPPORTED;
             plan->prec = precision;
@@ -407,7 +421,7 @@ lct_status lct_output_grid(lct_plan plan, int64_t index, double* y_reim, double*
 
 lct_status lct_input_grid(int64_t N, double* x) {
     if (!x) return LCT_ERR_ARG;
-    if (ilog2_exact(N) < 0) return LCT_ERR_N;
+    if (N < 2 || N > 65536) return LCT_ERR_N;
     for (int64_t k = 0; k < N; ++k)
         x[k] = M_PI * (double)(2 * k - N + 1) / (2.0 * std::sqrt(2.0 * (double)N));
     return LCT_OK;
@@ -473,9 +487,13 @@ lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_rei
     if (count < 0 || world < 1 || (count > 0 && (!N || !owner))) return LCT_ERR_ARG;
     std::vector<double> cost((size_t)count);
     for (int64_t s = 0; s < count; ++s) {
-        if (ilog2_exact(N[s]) < 0) return LCT_ERR_N;
+        if (N[s] < 2 || N[s] > 65536) return LCT_ERR_N;
         const bool diag = abcd_reim && abcd_reim[8 * s + 2] == 0.0 && abcd_reim[8 * s + 3] == 0.0;
-        cost[(size_t)s] = diag ? (double)N[s] : (double)N[s] * ilog2_exact(N[s]);
+        const int l = ilog2_exact(N[s]);
+        // a DFT of N (power of two), or two DFTs of M >= 2N - 1 (other N)
+        const double dft = l >= 0 ? (double)N[s] * l
+                                  : 2.0 * (double)((int64_t)1 << lct_blue_log2m(N[s])) * lct_blue_log2m(N[s]);
+        cost[(size_t)s] = diag ? (double)N[s] : dft;
     }
     std::vector<int64_t> order((size_t)count);
     std::iota(order.begin(), order.end(), (int64_t)0);
@@ -503,7 +521,9 @@ const char* lct_status_string(lct_status s) {
     switch (s) {
         case LCT_OK: return "ok";
         case LCT_ERR_ARG: return "invalid argument";
-        case LCT_ERR_N: return "N must be a power of two in [2, 65536]";
+        case LCT_ERR_N:
+            return "N must be a power of two in [2, 65536] or another N in [3, 8192] (complex64) / "
+                   "[3, 4096] (complex128)";
         case LCT_ERR_NOT_SYMPLECTIC: return "parameters do not satisfy ad - bc = 1";
         case LCT_ERR_DTYPE: return "unknown dtype";
         case LCT_ERR_ALIGN: return "pointer not aligned to the sample size";

@@ -49,6 +49,7 @@ struct lct_plan_s {
     // its idx list ordered by N, run through the chunk list chunks[chunk_off ..]
     struct group {
         int log2n, kind;
+        int n = 0;                  // N of the group's signals
         int64_t count, idx_off;
         int64_t tp_off = -1;
         int64_t chunk_off = 0, nchunks = 0;
@@ -91,6 +92,8 @@ typedef std::complex<double> cplx;
 // ---- lct_phase.cpp --------------------------------------------------------
 // log2 N for N a power of two in [2, 65536], else -1.
 int ilog2_exact(int64_t N);
+// Is this a plan of N that is not a power of two (chirp-convolution kernel)?
+inline bool blue_kind(int kind) { return kind == LCT_KIND_BLUE || kind == LCT_KIND_DIAGN; }
 // round(v 2^64) mod 2^64 for a turn fraction v (|v| < 1).
 uint64_t double_to_turns64(double v);
 // Validates p = {a, b, c, d} (re, im pairs; ad - bc = 1) and fills the

@@ -34,7 +34,7 @@ int main(void) {
     CHECK(lct_plan_destroy(p) == LCT_OK);
 
     /* validation errors are status codes */
-    CHECK(lct_plan_create(&p, 100, 1.0, 2.0, 0.5, 2.0, LCT_C64) == LCT_ERR_N);
+    CHECK(lct_plan_create(&p, 9000, 1.0, 2.0, 0.5, 2.0, LCT_C64) == LCT_ERR_N);   /* not a power of two, above 8192 */
     CHECK(lct_plan_create(&p, 64, 1.0, 2.0, 0.6, 2.0, LCT_C64) == LCT_ERR_NOT_SYMPLECTIC);
     CHECK(strcmp(lct_status_string(LCT_OK), "ok") == 0);
 

@@ -68,7 +68,7 @@ def test_input_grid_matches_oracle_nodes():
         assert np.allclose(x, O.nodes(N), rtol=1e-15, atol=1e-15)
 
 
-@pytest.mark.parametrize("N", [0, 1, 3, 100, 131072, -4])
+@pytest.mark.parametrize("N", [0, 1, 9000, 65535, 131072, -4])
 def test_bad_N(N):
     with pytest.raises(lct.LctError) as e:
         lct.lct_plan_create(N, 1.0, 2.0, 0.5, 2.0)
@@ -255,3 +255,68 @@ def test_phase_constants_exact(N, abcd):
     pre = dx / mpmath.sqrt(2j * mpmath.pi * B)
     t_c = -mpmath.mpf((N - 1) ** 2) / (4 * N) + mpmath.arg(pre) / (2 * mpmath.pi)
     assert abs(_turns_err(out_c, t_c, 64)) < 2 ** 14
+
+
+# --------------------------------------------------------------------------
+# N that is not a power of two (chirp-convolution kernel), host side
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,abcd", [(1000, (1.7, 0.21, (1.7 * -1.3 - 1) / 0.21, -1.3)),
+                                    (4095, (0.3, -1.9, (0.3 * 0.4 - 1) / -1.9, 0.4)),
+                                    (3, (1.0, 2.0, 0.5, 2.0))])
+def test_phase_constants_non_power_of_two(N, abcd):
+    """For N that is not a power of two the chirps absorb the -1/(8N) turns
+    of the convolution split: phi_in - 1/(8N), phi_out - 1/(8N), and the
+    constant is arg(dx / sqrt(2 pi i b)) alone (mpmath, 60 digits)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    a, b, c, d = abcd
+    p = lct.lct_plan_create(N, a, b, c, d)
+    try:
+        in_hi, in_lo, out_hi, out_lo, out_c = lct.lct_plan_phase_turns(p)
+    finally:
+        lct.lct_plan_destroy(p)
+    A, B, D = mpmath.mpf(a), mpmath.mpf(b), mpmath.mpf(d)
+    t_in = A * mpmath.pi / (32 * B * N) - mpmath.mpf(1) / (8 * N)
+    t_out = B * D / (2 * mpmath.pi * N) - mpmath.mpf(1) / (8 * N)
+    assert abs(_turns_err((in_hi << 64) | in_lo, t_in, 128)) < 2 ** 28
+    assert abs(_turns_err((out_hi << 64) | out_lo, t_out, 128)) < 2 ** 28
+    dx = mpmath.pi / mpmath.sqrt(2 * N)
+    pre = dx / mpmath.sqrt(2j * mpmath.pi * B)
+    assert abs(_turns_err(out_c, mpmath.arg(pre) / (2 * mpmath.pi), 64)) < 2 ** 14
+
+
+@pytest.mark.parametrize("N", [3, 100, 4095, 65535])
+def test_input_grid_any_n(N):
+    assert np.allclose(lct.lct_input_grid(N), O.nodes(N), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N,dtype,ok", [(4095, lct.LCT_C128, True), (4097, lct.LCT_C128, False),
+                                        (8191, lct.LCT_C64, True), (8193, lct.LCT_C64, False),
+                                        (3, lct.LCT_C64, True), (65535, lct.LCT_C64, False),
+                                        (1, lct.LCT_C64, False), (65537, lct.LCT_C64, False)])
+def test_non_power_of_two_sizes_accepted(N, dtype, ok):
+    if ok:
+        lct.Plan.create(N, 1.0, 2.0, 0.5, 2.0, dtype=dtype).destroy()
+        lct.Plan.batch([N, 64], [(1.0, 2.0, 0.5, 2.0)] * 2, [0, N], dtype=dtype).destroy()
+    else:
+        with pytest.raises(lct.LctError) as e:
+            lct.Plan.create(N, 1.0, 2.0, 0.5, 2.0, dtype=dtype)
+        assert e.value.status == 2
+
+
+def test_non_power_of_two_precision_choices():
+    p = lct.Plan.create(1000, 1.0, 2.0, 0.5, 2.0)
+    try:
+        for prec in (lct.LCT_PREC_PLAIN64, lct.LCT_PREC_PLAIN32, lct.LCT_PREC_SPLIT_BF16):
+            with pytest.raises(lct.LctError) as e:
+                p.set_precision(prec)
+            assert e.value.status == 10
+        p.set_precision(lct.LCT_PREC_NATIVE)
+    finally:
+        p.destroy()
+
+
+def test_partition_costs_non_power_of_two():
+    """A non-power-of-two N costs two DFTs of M >= 2N - 1 (here M = 2048)."""
+    owner, load = lct.lct_partition([1000, 1024], 2)
+    assert sorted(load.tolist()) == [1024 * 10, 2 * 2048 * 11]

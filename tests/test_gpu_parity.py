@@ -218,6 +218,108 @@ def test_plain64_complex64_io():
     assert rel_l2(G, ref).max() < 1e-6
 
 
+# --------------------------------------------------------------------------
+# N that is not a power of two: chirp - FFT_M - spectrum - inverse FFT_M -
+# chirp (M >= 2N - 1) in one kernel
+# --------------------------------------------------------------------------
+NON_POW2 = [3, 5, 6, 7, 12, 100, 1000, 4095]
+
+
+@pytest.mark.parametrize("N", NON_POW2 + [6000, 8191])
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_every_size_non_power_of_two(N, dtype):
+    if dtype == np.complex128 and N > 4096:
+        pytest.skip("complex128 takes N <= 4096 when N is not a power of two")
+    count = 37 if N <= 1024 else 5
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=200 + N, dtype=np.complex128)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    for abcd in [(0.37, -1.3, (0.37 * 0.8 - 1) / -1.3, 0.8), None]:
+        if abcd is None:       # per-signal parameters (batch plan)
+            p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code)
+            ref = O.lct(f.astype(dtype).astype(np.complex128), params)
+        else:
+            p = lct.Plan.create(N, *abcd, dtype=code)
+            ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+        try:
+            G = run(p.handle, f.astype(dtype), dtype)
+        finally:
+            p.destroy()
+        assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64), (N, abcd is None)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_non_power_of_two_b_zero_frft_and_complex(dtype):
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    tol = TOL32 if dtype == np.complex64 else TOL64
+    N = 300
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, 4, seed=31, dtype=np.complex128)
+    f = f.astype(dtype)
+    f64 = f.astype(np.complex128)
+    # b = 0
+    abcd = (1 / 1.3, 0.0, -0.7, 1.3)
+    p = lct.Plan.create(N, *abcd, dtype=code)
+    try:
+        assert rel_l2(run(p.handle, f, dtype), O.lct(f64, abcd)).max() < tol
+    finally:
+        p.destroy()
+    # fractional transform, z inside and on the unit circle
+    for z in [0.6 + 0.2j, np.exp(-0.9j)]:
+        xin = to_dev(f, dtype)
+        out = torch.empty_like(xin)
+        lct.frft_execute(N, z, xin, out, f.shape[0], code)
+        torch.cuda.synchronize()
+        assert rel_l2(out.cpu().numpy(), O.frft(f64, z)).max() < tol, z
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_ragged_mixed_powers_and_other_sizes(dtype):
+    """Powers of two and other N, b = 0 and b != 0, in one ragged plan."""
+    specs = [(None, 100, "lct", (0.5, 1.2, (0.5 * 0.4 - 1) / 1.2, 0.4)),
+             (None, 1000, "lct", (-1.1, -0.6, (-1.1 * 1.3 - 1) / -0.6, 1.3)),
+             (None, 256, "lct", (0.2, 0.9, (0.2 * -0.5 - 1) / 0.9, -0.5)),
+             (None, 100, "b0", (1 / 0.8, 0.0, 0.6, 0.8)),
+             (None, 7, "lct", (0.0, 1.0, -1.0, 0.0)),
+             (None, 4095, "frft", 0.7 * np.exp(1.2j)),
+             (None, 64, "b0", (1 / 1.5, 0.0, -0.2, 1.5)),
+             (None, 100, "lct", (1.4, -1.8, (1.4 * 0.3 - 1) / -1.8, 0.3))]
+    rng = np.random.default_rng(77)
+    Ns, abcds, offs, sigs = [], [], [], []
+    off = 3
+    for _, N, kind, prm in specs:
+        abcd = O.abcd_of_z(prm) if kind == "frft" else np.asarray(prm, dtype=np.complex128)
+        x = O.nodes(N)
+        f = np.exp(-x * x / 8) * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+        Ns.append(N)
+        abcds.append(abcd)
+        offs.append(off)
+        sigs.append(f)
+        off += N + 5
+    buf = np.zeros(off, dtype=np.complex128)
+    for o, f in zip(offs, sigs):
+        buf[o:o + len(f)] = f
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    p = lct.Plan.batch(Ns, np.array(abcds), offs, dtype=code)
+    try:
+        x = torch.from_numpy(buf.astype(dtype)).cuda()
+        out = torch.zeros_like(x)
+        lct.lct_execute(p.handle, x, out, len(Ns))
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        G = out.cpu().numpy()
+    finally:
+        p.destroy()
+    tol = TOL32 if dtype == np.complex64 else TOL64
+    for N, abcd, o, f in zip(Ns, abcds, offs, sigs):
+        ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+        assert rel_l2(G[o:o + N], ref) < tol, (N, abcd)
+    mask = np.ones(len(buf), dtype=bool)
+    for N, o in zip(Ns, offs):
+        mask[o:o + N] = False
+    assert np.all(G[mask] == 0)
+
+
 @pytest.mark.parametrize("N", [256, 4096])
 def test_plain32_complex64(N):
     """The unfused FP32 baseline (FP32 chirps around cuFFT C2C)."""

@@ -139,6 +139,6 @@ def test_partition_properties():
     _, loadb = lct.lct_partition(Ns, 1, abcd)
     assert np.isclose(loadb[0], cost.sum() - cost[2] + Ns[2])
     with pytest.raises(lct.LctError):
-        lct.lct_partition(np.array([100]), 2)            # not a power of two
+        lct.lct_partition(np.array([70000]), 2)          # above 65536
     with pytest.raises(lct.LctError):
         lct.lct_partition(Ns, 0)
