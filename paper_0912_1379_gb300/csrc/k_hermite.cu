@@ -24,12 +24,16 @@
 namespace {
 
 // Number of eigenvalues of H below lam (Sturm count by the LDL^T pivots).
+// A zero pivot is replaced by a tiny negative one before it is counted (the
+// count of a lam perturbed by that much), so every pivot is counted with
+// the sign the next step divides by.
 __device__ int sturm_count(int n, double lam) {
     double q = -lam;
+    if (q == 0.0) q = -1e-300;
     int c = q < 0.0;
     for (int i = 1; i < n; ++i) {
-        if (q == 0.0) q = -1e-300;
         q = -lam - (0.5 * (double)i) / q;
+        if (q == 0.0) q = -1e-300;
         c += q < 0.0;
     }
     return c;
