@@ -783,6 +783,17 @@ FP64_NOMINAL_TFLOPS = 1.25            # GB300 FP64 (nominal, CUDA cores)
 FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured BF16 burst rate times the nominal
+    TF32/BF16 ratio (1.1 / 2.25 PFLOP/s), else the nominal 1.1 PFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = float(json.load(fh)["bf16_tflops"])
+        return bf16 * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16 (1.1/2.25)"
+    except Exception:
+        return 1100.0, "nominal dense tf32"
+
+
 def hermite_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     """F_z = sqrt(2 pi) U^T D(z) U applied to a batch of signals sampled at
     the zeros of H_N: two real-by-complex products of N x N by N x batch
@@ -811,9 +822,21 @@ def hermite_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
         steps = max(3, min(args.steps, 10)) if name == "c128" else args.steps
         ms, ck = timed_loop(torch, step, steps, stream, local, barrier, max_over_ranks, args.no_clocks)
         flops = 8.0 * N * N * B
-        peak = FP64_NOMINAL_TFLOPS if name == "c128" else FP32_DERIVED_TFLOPS
-        res[name] = {"ms": ms, "steps": steps, "tflops": flops / (ms * 1e-3) / 1e12,
-                     "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak, "clocks": ck}
+        if name == "c128":
+            res[name] = {"ms": ms, "steps": steps, "tflops": flops / (ms * 1e-3) / 1e12,
+                         "peak_tflops": FP64_NOMINAL_TFLOPS,
+                         "frac": flops / (ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                         "kernel": "k_herm_gemm<double> (CUDA cores)", "clocks": ck}
+        else:
+            # tensor cores: split TF32, three products per useful one
+            tf32_peak = tf32_peak_tflops()
+            tensor = 3.0 * flops / (ms * 1e-3) / 1e12
+            res[name] = {"ms": ms, "steps": steps, "tflops": flops / (ms * 1e-3) / 1e12,
+                         "tensor_tflops": tensor, "peak_tflops": tf32_peak[0],
+                         "peak_kind": tf32_peak[1], "frac": tensor / tf32_peak[0],
+                         "fp32_simt_peak_tflops": FP32_DERIVED_TFLOPS,
+                         "kernel": "k_herm_umma (tcgen05.mma kind::tf32, 3 split products)",
+                         "clocks": ck}
         if clocks is None:
             clocks = ck
         outs[name] = d_out[:64].cpu().numpy()

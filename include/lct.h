@@ -218,9 +218,14 @@ lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, voi
  * bisection on Sturm counts, vectors by the three-term recurrence -- and
  * cached for the life of the process; that first call synchronises.  Each
  * call takes a workspace of batch * N + N samples from the stream-ordered
- * allocator on `stream` and returns it there.  complex128: FP64 arithmetic;
- * complex64: FP32 arithmetic with U rounded to FP32.  Asynchronous on
- * `stream` after the first call for an N. */
+ * allocator on `stream` and returns it there.  complex128: FP64 arithmetic
+ * on the CUDA cores.  complex64: for N >= 128 the two products run on the
+ * tensor cores (tcgen05, kind::tf32) with both operands split into TF32
+ * hi + lo parts and three products accumulated in FP32 (relative error
+ * about 1e-7; the split operands of U, 2 x 4 N^2 bytes rounded up to whole
+ * tiles, are added to the cache at the first such call); below N = 128, FP32
+ * CUDA-core arithmetic.  Asynchronous on `stream` after the first call for
+ * an N. */
 lct_status frft_hermite_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                                 int64_t batch, lct_dtype dtype, lct_stream_t stream);
 /* The nodes x_k (ascending, N doubles into host memory x) and, if U is not
@@ -228,6 +233,11 @@ lct_status frft_hermite_execute(int64_t N, double z_re, double z_im, const void*
  * component n of u_k) of the Hermite-zero transform above, computed on the
  * current device (built there if needed; synchronises). */
 lct_status frft_hermite_basis(int64_t N, double* x, double* U);
+/* Synchronise `stream`, then read and clear the status word of the
+ * Hermite-zero tensor-core kernels: LCT_ERR_TIMEOUT if one of their bounded
+ * waits (bulk copy or MMA completion, 2 s) gave up since the last call (its
+ * output is then not written), else LCT_OK. */
+lct_status frft_hermite_status(lct_stream_t stream);
 
 /* Backward pass of lct_execute (spec differentiation; the chain rule
  * on L = S1 F S2 of Sec. 3).  grad_out: cotangent g = dl/dRe G + i dl/dIm G

@@ -71,6 +71,7 @@ def _load():
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "frft_hermite_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "frft_hermite_basis": [i64, dp, dp],
+            "frft_hermite_status": [vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
             "lct_plan_phase_turns": [vp, i64, up],
@@ -277,6 +278,12 @@ def frft_hermite_execute(N: int, z: complex, inp, out, batch: int, dtype: int = 
     z = complex(z)
     _check(_load().frft_hermite_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
                                         _stream_handle(stream)), "frft_hermite_execute")
+
+
+def frft_hermite_status(stream=None) -> int:
+    """Synchronise and return the Hermite tensor-core kernels' status (0 = ok,
+    9 = a bounded wait gave up); does not raise."""
+    return int(_load().frft_hermite_status(_stream_handle(stream)))
 
 
 def frft_hermite_basis(N: int, with_matrix: bool = True):

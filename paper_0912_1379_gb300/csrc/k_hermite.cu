@@ -18,8 +18,20 @@
 //  * k_herm_gemm: out[b][j] = alpha_j sum_k A[b][k] B(k, j), A complex
 //    (the signals), B real (U or U^T), one 32-signal x 64-column tile per
 //    CTA; the first product T = f U^T takes alpha_n = sqrt(2 pi) z^n, the
-//    second F_z f = T U takes alpha = 1.
+//    second F_z f = T U takes alpha = 1 (FP64, and FP32 below N = 128).
+//  * k_herm_umma: the same two products for complex64 on the tensor cores
+//    (tcgen05.mma kind::tf32, accumulator in tensor memory), each operand
+//    split into TF32 hi + lo parts and three products hi.hi + hi.lo + lo.hi
+//    accumulated in FP32 (relative error about 1e-7).  A 128 x 256 output
+//    tile per CTA: rows are 64 signals x (re, im) -- a complex-by-real
+//    product is two real ones -- and columns 256 outputs; K runs over N in
+//    chunks of 32 through two shared-memory stages, so one chunk's MMAs run
+//    while the next chunk is staged.  B (U or U^T) is split and tiled once
+//    per basis (k_umma_pack) and arrives by one bulk copy per chunk.
 #include "xft_common.cuh"
+#include "xft_umma.cuh"
+
+__device__ int32_t g_herm_status;      // bounded waits of k_herm_umma that gave up
 
 namespace {
 
@@ -166,6 +178,268 @@ k_herm_gemm(const cpx<R>* __restrict__ A, const R* __restrict__ Bm, cpx<R>* __re
     }
 }
 
+// alpha_m = sqrt(2 pi) z^m: |z|^m = e^{m log|z|}, and the angle m arg(z) in
+// turns, reduced exactly: t = arg(z)/(2 pi) arrives as a double-double
+// (t_hi + t_lo), m t_hi is split into a double-double by an FMA, and only
+// the fractional part (to 2^-53 turns) reaches sincospi.  zero: z = 0
+// (alpha = sqrt(2 pi) at m = 0, else 0).
+template <class R>
+__global__ void k_herm_alpha(int n, double t_hi, double t_lo, double log_r, int zero,
+                             cpx<R>* __restrict__ alpha) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const double s2pi = 2.5066282746310002;
+    if (zero) {
+        alpha[m] = {m == 0 ? (R)s2pi : R(0), R(0)};
+        return;
+    }
+    const double p = (double)m * t_hi;
+    const double pe = fma((double)m, t_hi, -p);        // m t_hi = p + pe exactly
+    const double fp = p - rint(p);                      // exact
+    double f = fp + (pe + (double)m * t_lo);
+    f -= rint(f);                                       // turns in [-1/2, 1/2]
+    double sn, cs;
+    sincospi(2.0 * f, &sn, &cs);
+    const double mag = m == 0 ? s2pi : s2pi * exp((double)m * log_r);
+    alpha[m] = {(R)(mag * cs), (R)(mag * sn)};
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core form (complex64)
+// ---------------------------------------------------------------------------
+constexpr int kUM = 128, kUN = 256, kUK = 32, kUThreads = 256;
+constexpr uint32_t kUASz = kUM * kUK * 4;            // one part (hi or lo) of an A chunk
+constexpr uint32_t kUBSz = kUN * kUK * 4;            // one part of a B chunk
+constexpr uint32_t kUStage = 2 * kUASz + 2 * kUBSz;  // A hi, A lo, B hi, B lo
+constexpr uint32_t kUSmem = 2 * kUStage;
+constexpr uint32_t kUTmemCols = 256;
+constexpr uint64_t kUWaitNs = 2000000000ull;
+constexpr uint32_t kULbo = 128, kUSbo = kUK * 32;    // core matrices along K / next 8 rows
+
+// Split and tile B for the tensor-core product: block (jt, kc) of the output
+// holds, for output columns j = 256 jt + r and inputs k = 32 kc + q, the TF32
+// hi part of B(k, j) then its lo part, each in the K-major core-matrix
+// layout of umma::tf32_offset.  trans = 1: B(k, j) = U[j][k] (first
+// product); trans = 0: B(k, j) = U[k][j].  Zero outside n x n.
+__global__ void k_umma_pack(const double* __restrict__ U, int n, int trans, int kc_count,
+                            float* __restrict__ out, int64_t total) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t % kUK);
+        const int r = (int)((t / kUK) % kUN);
+        const int64_t blk = t / (kUK * kUN);          // jt * kc_count + kc
+        const int kc = (int)(blk % kc_count), jt = (int)(blk / kc_count);
+        const int j = jt * kUN + r, k = kc * kUK + q;
+        double v = 0.0;
+        if (j < n && k < n) v = trans ? U[(int64_t)j * n + k] : U[(int64_t)k * n + j];
+        const float hi = umma::to_tf32((float)v);
+        const float lo = umma::to_tf32((float)(v - (double)hi));
+        float* base = out + blk * (int64_t)(2 * kUBSz / 4);
+        const uint32_t off = umma::tf32_offset((uint32_t)r, (uint32_t)q, kUK) / 4;
+        base[off] = hi;
+        base[kUBSz / 4 + off] = lo;
+    }
+}
+
+__device__ __forceinline__ void record_umma_timeout() {
+    atomicCAS(&g_herm_status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
+}
+
+// Accumulation: a tcgen05 accumulator that takes every K step of a long
+// product loses accuracy (its FP32 additions measured as truncating: 1e-5
+// relative at N = 1024 instead of 5e-7), so each 32-wide K chunk goes to a
+// fresh accumulator, one of two in tensor memory (chunk c to accumulator
+// c & 1, 2 x 256 columns), and is then added into FP32 register sums with
+// round-to-nearest while the tensor cores fill the other accumulator.
+// 8 warps: warp w reads TMEM lanes 32 (w & 3) .. + 31 (rows) and columns
+// 128 (w >> 2) .. + 127, and keeps those 128 sums.
+__device__ __forceinline__ void umma_drain(uint32_t taddr, float* sum) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float v[16];
+        umma::tmem_ld16(taddr + 16 * q, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sum[16 * q + i] += v[i];
+    }
+}
+
+__global__ void __launch_bounds__(kUThreads, 1)
+k_herm_umma(const cpx<float>* __restrict__ A, const float* __restrict__ Bblk,
+            cpx<float>* __restrict__ C, const cpx<float>* __restrict__ alpha, int64_t batch, int n,
+            int kc_count) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int jt = blockIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * (kUM / 2);
+    if (warp == 0) umma::tmem_alloc(&tmem_slot, 2 * kUTmemCols);
+    if (tid == 0) {
+        xasync::mbar_init(&bar_b[0], 1);
+        xasync::mbar_init(&bar_b[1], 1);
+        xasync::mbar_init(&bar_mma[0], 1);
+        xasync::mbar_init(&bar_mma[1], 1);
+        xasync::fence_mbar_init();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    // this thread's view of accumulator a: lane 32 quad + lane, columns 128 half ..
+    const uint32_t my_acc = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(128 * half);
+    constexpr uint32_t idesc = umma::instr_desc(umma::kFmtTF32, umma::kFmtTF32, kUM, kUN);
+    float sum[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) sum[i] = 0.f;
+    bool ok = true;
+    int c = 0;
+    for (; c < kc_count; ++c) {
+        const int s = c & 1;
+        unsigned char* st = sm + s * kUStage;
+        float* a_hi = reinterpret_cast<float*>(st);
+        float* a_lo = reinterpret_cast<float*>(st + kUASz);
+        float* b_hi = reinterpret_cast<float*>(st + 2 * kUASz);
+        // chunk c - 2 (stage s, accumulator s) complete: drain it, then reuse
+        if (c >= 2) {
+            if (tid == 0) ok = xasync::mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, kUWaitNs);
+            if (!__syncthreads_and(ok)) break;
+            umma::fence_after_sync();
+            umma_drain(my_acc + (uint32_t)(s * kUTmemCols), sum);
+            umma::fence_before_sync();
+        }
+        if (tid == 0) {
+            xasync::mbar_arrive_expect_tx(&bar_b[s], 2 * kUBSz);
+            xasync::bulk_g2s(b_hi, Bblk + ((int64_t)jt * kc_count + c) * (2 * kUBSz / 4), 2 * kUBSz,
+                             &bar_b[s]);
+        }
+        // A chunk: signal bb = tid / 4, inputs k = 32 c + 8 (tid & 3) + 0..7;
+        // row 2 bb holds the real parts, row 2 bb + 1 the imaginary parts
+        {
+            const int bb = tid >> 2, kq = (tid & 3) * 8;
+            const int64_t b = b0 + bb;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                float re[4], im[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = c * kUK + kq + 4 * g + e;
+                    cpx<float> v = {0.f, 0.f};
+                    if (b < batch && k < n) v = A[b * n + k];
+                    re[e] = v.x;
+                    im[e] = v.y;
+                }
+                const uint32_t o_re = umma::tf32_offset(2 * bb, kq + 4 * g, kUK) / 4;
+                const uint32_t o_im = umma::tf32_offset(2 * bb + 1, kq + 4 * g, kUK) / 4;
+                float4 h, l;
+                h.x = umma::to_tf32(re[0]); l.x = umma::to_tf32(re[0] - h.x);
+                h.y = umma::to_tf32(re[1]); l.y = umma::to_tf32(re[1] - h.y);
+                h.z = umma::to_tf32(re[2]); l.z = umma::to_tf32(re[2] - h.z);
+                h.w = umma::to_tf32(re[3]); l.w = umma::to_tf32(re[3] - h.w);
+                *reinterpret_cast<float4*>(a_hi + o_re) = h;
+                *reinterpret_cast<float4*>(a_lo + o_re) = l;
+                h.x = umma::to_tf32(im[0]); l.x = umma::to_tf32(im[0] - h.x);
+                h.y = umma::to_tf32(im[1]); l.y = umma::to_tf32(im[1] - h.y);
+                h.z = umma::to_tf32(im[2]); l.z = umma::to_tf32(im[2] - h.z);
+                h.w = umma::to_tf32(im[3]); l.w = umma::to_tf32(im[3] - h.w);
+                *reinterpret_cast<float4*>(a_hi + o_im) = h;
+                *reinterpret_cast<float4*>(a_lo + o_im) = l;
+            }
+        }
+        xasync::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            ok = xasync::mbar_wait(&bar_b[s], (c >> 1) & 1, kUWaitNs);
+            if (!ok) {
+                // give up on this chunk, but let its copy land before leaving
+                record_umma_timeout();
+                xasync::mbar_wait(&bar_b[s], (c >> 1) & 1, kUWaitNs);
+            } else {
+                umma::fence_after_sync();
+                const uint32_t ah = xasync::smem_addr(a_hi), al = ah + kUASz;
+                const uint32_t bh = ah + 2 * kUASz, bl = bh + kUBSz;
+                const uint32_t d = tmem + (uint32_t)(s * kUTmemCols);
+#pragma unroll
+                for (int ks = 0; ks < kUK / 8; ++ks) {
+                    const uint32_t o = ks * 2 * kULbo;          // 8 K values = 2 core matrices
+                    const uint64_t dah = umma::smem_desc(ah + o, kULbo, kUSbo);
+                    const uint64_t dal = umma::smem_desc(al + o, kULbo, kUSbo);
+                    const uint64_t dbh = umma::smem_desc(bh + o, kULbo, kUSbo);
+                    const uint64_t dbl = umma::smem_desc(bl + o, kULbo, kUSbo);
+                    umma::mma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    umma::mma_tf32(d, dah, dbl, idesc, 1u);
+                    umma::mma_tf32(d, dal, dbh, idesc, 1u);
+                }
+                umma::commit(&bar_mma[s]);
+            }
+        }
+        if (!__syncthreads_and(ok)) break;          // chunk c was not issued
+    }
+    // chunks 0 .. c-1 were issued; the last two are still to be drained (all
+    // issued MMAs complete before the CTA leaves; a failed wait skips the
+    // epilogue)
+    if (!ok && tid == 0) record_umma_timeout();
+    for (int t = c - 2 < 0 ? 0 : c - 2; t < c; ++t) {
+        bool w = true;
+        if (tid == 0) {
+            w = xasync::mbar_wait(&bar_mma[t & 1], (t >> 1) & 1, kUWaitNs);
+            if (!w) record_umma_timeout();
+        }
+        ok = __syncthreads_and(w) && ok;
+        umma::fence_after_sync();
+        if (ok) umma_drain(my_acc + (uint32_t)((t & 1) * kUTmemCols), sum);
+    }
+    ok = ok && c == kc_count;
+    if (ok) {
+        // row m = 32 quad + lane = 2 bb + part of signal b0 + bb; the even lane
+        // stores the first 64 of this warp's 128 columns, the odd lane the rest
+        const int m = 32 * quad + lane;
+        const int64_t b = b0 + (m >> 1);
+        const bool odd = (m & 1) != 0;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            const float send0 = sum[i], send1 = sum[64 + i];
+            const float got0 = __shfl_xor_sync(0xffffffffu, send0, 1);
+            const float got1 = __shfl_xor_sync(0xffffffffu, send1, 1);
+            // even lane: column i (re = own, im = partner); odd lane: column 64 + i
+            const float re = odd ? got1 : send0;
+            const float im = odd ? send1 : got0;
+            const int j = jt * kUN + 128 * half + (odd ? 64 + i : i);
+            if (b < batch && j < n) {
+                cpx<float> r = {re, im};
+                if (alpha) r = cmul(r, alpha[j]);
+                C[b * n + j] = r;
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, 2 * kUTmemCols);
+}
+
+cudaError_t umma_apply(int n, const void* in, void* out, void* work, const void* alpha,
+                       const float* B1, const float* B2, int64_t batch, cudaStream_t stream) {
+    static int attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_herm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUSmem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = 1;
+    }
+    const int kc = (n + kUK - 1) / kUK;
+    const dim3 grid((unsigned)((n + kUN - 1) / kUN), (unsigned)((batch + kUM / 2 - 1) / (kUM / 2)));
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    k_herm_umma<<<grid, kUThreads, kUSmem, stream>>>((const cpx<float>*)in, B1, (cpx<float>*)work,
+                                                     (const cpx<float>*)alpha, batch, n, kc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_herm_umma<<<grid, kUThreads, kUSmem, stream>>>((const cpx<float>*)work, B2, (cpx<float>*)out,
+                                                     nullptr, batch, n, kc);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t herm_apply(int n, const void* in, void* out, void* work, const void* alpha,
                        const void* U, int64_t batch, cudaStream_t stream) {
@@ -200,4 +474,46 @@ cudaError_t lct_launch_hermite_apply(int dtype, int n, const void* in, void* out
                                      cudaStream_t stream) {
     if (dtype == 0) return herm_apply<float>(n, in, out, work, alpha, U, batch, stream);
     return herm_apply<double>(n, in, out, work, alpha, U, batch, stream);
+}
+
+// Bytes of one split, tiled B operand of the tensor-core product for N = n.
+size_t lct_hermite_umma_bytes(int n) {
+    const size_t jt = (size_t)((n + kUN - 1) / kUN), kc = (size_t)((n + kUK - 1) / kUK);
+    return jt * kc * 2 * (size_t)kUBSz;
+}
+
+cudaError_t lct_launch_hermite_umma_pack(int n, const double* U, float* B1, float* B2,
+                                         cudaStream_t stream) {
+    const int kc = (n + kUK - 1) / kUK;
+    const int64_t total = (int64_t)((n + kUN - 1) / kUN) * kc * kUN * kUK;
+    const unsigned grid = (unsigned)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+    k_umma_pack<<<grid, 256, 0, stream>>>(U, n, 1, kc, B1, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_umma_pack<<<grid, 256, 0, stream>>>(U, n, 0, kc, B2, total);
+    return cudaGetLastError();
+}
+
+cudaError_t lct_launch_hermite_apply_umma(int n, const void* in, void* out, void* work,
+                                          const void* alpha, const float* B1, const float* B2,
+                                          int64_t batch, cudaStream_t stream) {
+    return umma_apply(n, in, out, work, alpha, B1, B2, batch, stream);
+}
+
+// Read and clear the status word of the tensor-core kernels (synchronises).
+cudaError_t lct_hermite_read_status(int32_t* v) {
+    cudaError_t e = cudaMemcpyFromSymbol(v, g_herm_status, sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    const int32_t zero = 0;
+    return cudaMemcpyToSymbol(g_herm_status, &zero, sizeof(int32_t));
+}
+
+cudaError_t lct_launch_hermite_alpha(int dtype, int n, double t_hi, double t_lo, double log_r,
+                                     int zero, void* alpha, cudaStream_t stream) {
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (dtype == 0)
+        k_herm_alpha<float><<<grid, 256, 0, stream>>>(n, t_hi, t_lo, log_r, zero, (cpx<float>*)alpha);
+    else
+        k_herm_alpha<double><<<grid, 256, 0, stream>>>(n, t_hi, t_lo, log_r, zero, (cpx<double>*)alpha);
+    return cudaGetLastError();
 }

@@ -71,13 +71,17 @@ def test_transform_matches_oracle_fp64(N, z):
     assert rel_l2(got, ref).max() < TOL64
 
 
-@pytest.mark.parametrize("N", [64, 1024])
+@pytest.mark.parametrize("N", [64, 128, 300, 1024, 2048])
 @pytest.mark.parametrize("z", [np.exp(-0.7j), 0.8 * np.exp(2.1j)])
 def test_transform_matches_oracle_fp32(N, z):
-    f = signals(N, 40, seed=N + 1)
+    """complex64: CUDA cores below N = 128, else the tensor cores (split
+    TF32, 64-signal x 256-column tiles: 70 signals and N = 300 leave partial
+    tiles in both directions)."""
+    f = signals(N, 70, seed=N + 1)
     _, F = H.hermite_zero_frft(N, z)
     ref = f.astype(np.complex64).astype(np.complex128) @ F.T
     got = apply(N, z, f, np.complex64)
+    assert lct.frft_hermite_status() == 0
     assert rel_l2(got, ref).max() < TOL32
 
 
