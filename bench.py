@@ -89,13 +89,14 @@ def parse():
                          "on the tensor cores")
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "ragged", "fields2d", "backward", "config0", "uniform1024",
-                             "hermite"],
+                             "hermite", "nonpow2"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
                          "instances in one graph launch; fields2d: separable 2-D LCT forward + "
                          "backward on 8 fields of 2048 x 2048; backward: lct_backward (adjoint "
                          "+ per-signal parameter gradients) on the 16384 x N=4096 batch; config0: "
                          "12 x N=256 complex128 latency; uniform1024: 4096 x N=1024 (L2 flushed); "
-                         "hermite: the Hermite-zero FrFT of eq. (tmat), 4096 x N=1024")
+                         "hermite: the Hermite-zero FrFT of eq. (tmat), 4096 x N=1024; nonpow2: "
+                         "16384 x N=3000")
     return ap.parse_args()
 
 
@@ -879,6 +880,60 @@ def hermite_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
 
 
 # ---------------------------------------------------------------------------
+# N that is not a power of two (chirp convolution of length M >= 2N - 1)
+# ---------------------------------------------------------------------------
+def nonpow2_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
+    """16384 complex64 signals of N = 3000 (M = 8192), G1 per-signal
+    parameters; one step = one lct_execute (the fused chirp-convolution
+    kernel: pre-chirp, FFT_M, spectrum, inverse FFT_M, post-chirp)."""
+    N, count = 3000, 16384
+    x = lct.lct_input_grid(N)
+    params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + 31 + rank, dtype=np.complex64)
+    plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(f).cuda()
+    d_out = torch.empty_like(d_in)
+
+    def step():
+        plan.execute(d_in, d_out, count, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if lct.lct_device_status(plan.handle) != 0:
+        raise RuntimeError("device status after warm-up")
+    ms, clocks = timed_loop(torch, step, args.steps, stream, local, barrier, max_over_ranks,
+                            args.no_clocks)
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, nsig, dt, cores, ref = cpu_oracle_rate(x, params, f, min_seconds=10.0)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d signals of the %d x N=%d workload, %.1f s" % (nsig, count, N, dt)}
+        accuracy = accuracy_block(rel_l2_rows(d_out[:nsig].cpu().numpy(), ref),
+                                  "FP64 oracle on the cpu_baseline sample")
+    plan.destroy()
+    pts = count * N
+    peak, peak_kind = measured_peak()
+    achieved = pts * BYTES_PER_POINT / (ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "LCT points/s at N=3000 (not a power of two), 16384 signals complex64; %HBM",
+            "value": world * pts / (ms * 1e-3), "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "nonpow2: 16384 x N=3000 complex64, G1 per-signal (a,b,c,d)",
+                       "M": 8192, "l2": "inputs larger than L2 (393 MB per buffer), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_xft_blue<13, float> (16 B/point; two FFTs of M = 8192 per signal)"},
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -910,7 +965,8 @@ def main():
         return float(t.item())
 
     arms = {"ragged": ragged_arm, "fields2d": fields2d_arm, "backward": backward_arm,
-            "config0": config0_arm, "uniform1024": uniform1024_arm, "hermite": hermite_arm}
+            "config0": config0_arm, "uniform1024": uniform1024_arm, "hermite": hermite_arm,
+            "nonpow2": nonpow2_arm}
     if args.workload in arms:
         arms[args.workload](args, rank, world, lct, torch, barrier, max_over_ranks, local)
         if dist is not None:

@@ -25,9 +25,12 @@ struct blue_shape {
     static constexpr int THREADS = T * SPC;
 };
 
+// Resident threads per SM the register budget is sized for: 512 (128
+// registers a thread below 1024-thread CTAs) -- the two DFTs of this kernel
+// need more than the single-DFT kernel's 64.
 template <int L, class R>
 constexpr int blue_min_blocks() {
-    constexpr int per_sm = sizeof(R) == 4 ? 1024 : 512;
+    constexpr int per_sm = 512;
     constexpr int b = per_sm / blue_shape<L>::THREADS;
     return b > 0 ? b : 1;
 }
@@ -65,45 +68,64 @@ k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     const int64_t sig = (int64_t)blockIdx.x * F::SPC + sl;
     bool active = sig < count;
     const int64_t gsig = idx ? (active ? idx[sig] : 0) : sig;
-    const lct_desc D = desc[desc_step && active ? gsig : 0];
-    if (active && (D.kind != LCT_KIND_BLUE || D.n != n || D.log2n != L || D.offset < 0)) {
+    const lct_desc* Dp = desc + (desc_step && active ? gsig : 0);
+    if (active && (Dp->kind != LCT_KIND_BLUE || Dp->n != n || Dp->log2n != L || Dp->offset < 0)) {
         if (i == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
         active = false;
     }
-    const int64_t base = desc_step ? D.offset : sig * (int64_t)n;
+    const int64_t base = desc_step ? Dp->offset : sig * (int64_t)n;
     buf += sl * S::NP;
-    const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
 
     cpx<R> v[S::E];
-    // load samples k < N with the pre-chirp; the rest of the tile is zero
+    // load samples k < N with the pre-chirp; the rest of the tile is zero.
+    // (The descriptor is read where it is used, not held in registers across
+    // the two DFTs, which would spill at this register budget.)
+    {
+        const uint64_t in_hi = Dp->in_hi, in_lo = Dp->in_lo;
+        const bool decay = (Dp->flags & LCT_FLAG_DECAY) != 0;
+        const double dec = Dp->decay;
 #pragma unroll
-    for (int e = 0; e < S::E; ++e) {
-        const int k = i + e * S::T;
-        cpx<R> f = {R(0), R(0)};
-        if (active && k < n) {
-            f = ld_stream(in + base + k);
-            cpx<R> w = chirp_any<R>(D.in_hi, D.in_lo, 0, k, n);
-            if (decay) {
-                const uint32_t m2 = m_squared(k, n);
-                if constexpr (sizeof(R) == 4) w = cscale(w, expf(-(float)D.decay * (float)m2));
-                else w = cscale(w, exp(-D.decay * (double)m2));
+        for (int e = 0; e < S::E; ++e) {
+            const int k = i + e * S::T;
+            cpx<R> f = {R(0), R(0)};
+            if (active && k < n) {
+                f = ld_stream(in + base + k);
+                cpx<R> w = chirp_any<R>(in_hi, in_lo, 0, k, n);
+                if (decay) {
+                    const uint32_t m2 = m_squared(k, n);
+                    if constexpr (sizeof(R) == 4) w = cscale(w, expf(-(float)dec * (float)m2));
+                    else w = cscale(w, exp(-dec * (double)m2));
+                }
+                f = cmul(f, w);
             }
-            f = cmul(f, w);
+            v[e] = f;
         }
-        v[e] = f;
     }
-    dft_signal<L, -1>(v, buf, i, tw);
-    // circular convolution with h: times its spectrum (already divided by M)
+    // Circular convolution with h: DFT_M, times the spectrum of h (already
+    // divided by M), inverse DFT_M.  The inverse is taken as
+    // conj(DFT_M(conj(.))), so both transforms are the same forward DFT run
+    // by a two-trip loop the compiler keeps rolled: one copy of the engine's
+    // code, and the register footprint of a single DFT.
+#pragma unroll 1
+    for (int round = 0; round < 2; ++round) {
+        dft_signal<L, -1>(v, buf, i, tw);
+        if (round == 0) {
 #pragma unroll
-    for (int e = 0; e < S::E; ++e) v[e] = cmul(v[e], ld_spec<R>(spec + i + e * S::T));
-    __syncthreads();                  // the forward DFT's last exchange is fully read
-    dft_signal<L, +1>(v, buf, i, tw);
+            for (int e = 0; e < S::E; ++e) {
+                const cpx<R> y = cmul(v[e], ld_spec<R>(spec + i + e * S::T));
+                v[e] = {y.x, -y.y};
+            }
+            __syncthreads();          // the first DFT's last exchange is fully read
+        }
+    }
     if (active) {
-        const R sc = (R)D.scale;
+        const uint64_t out_hi = Dp->out_hi, out_lo = Dp->out_lo, out_c = Dp->out_c;
+        const R sc = (R)Dp->scale;
 #pragma unroll
         for (int e = 0; e < S::E; ++e) {
             const int j = i + e * S::T;
-            if (j < n) out[base + j] = cscale(cmul(v[e], chirp_any<R>(D.out_hi, D.out_lo, D.out_c, j, n)), sc);
+            const cpx<R> y = {v[e].x, -v[e].y};         // the conj of the inverse's form
+            if (j < n) out[base + j] = cscale(cmul(y, chirp_any<R>(out_hi, out_lo, out_c, j, n)), sc);
         }
     }
 }

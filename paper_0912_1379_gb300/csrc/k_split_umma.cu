@@ -1,0 +1,257 @@
+// Split-precision XFT on the 5th-generation tensor cores (tcgen05), N = 4096
+// complex64: the three radix-16 passes of the Stockham plan run as products
+// of the real 32 x 32 DFT matrix on the tcgen05.mma pipe (kind::f16 with
+// BF16 operands, FP32 accumulators in tensor memory); chirps, twiddles and
+// the exchanges between passes stay on the CUDA cores, with the exact
+// fixed-point chirp phases of the native path.
+//
+// One radix-16 DFT y_j = sum_e u_e e^{-2 pi i j e / 16} of a group of 16
+// samples is the real product  D[g][n] = sum_k A[g][k] B[k][n]  with
+//   A[g][2e + c]  = (Re, Im)_c u_e             (the group's 32 inputs)
+//   B[2e][2j] = Re F_je,  B[2e+1][2j] = -Im F_je,
+//   B[2e][2j+1] = Im F_je, B[2e+1][2j+1] = Re F_je   (F_je = e^{-2 pi i je/16})
+// so D[g][2j + c] = (Re, Im)_c y_j.  A signal's 256 groups are two M = 128
+// tiles; N = 32, K = 32 (two K = 16 steps); each operand is split into BF16
+// hi + lo parts and the product taken as hi.hi + hi.lo + lo.hi: 12 MMAs per
+// pass, issued by one thread and committed to an mbarrier.
+//
+// Data flow of one CTA (256 threads, one signal at a time, persistent):
+// thread t owns TMEM lane t, i.e. row t of the accumulator.  Pass 0: thread t
+// loads samples t + 256 e with the pre-chirp, splits them and writes A row t.
+// After the MMAs of pass p, thread t reads its row -- the 16 outputs of its
+// group -- and, for p < 2, applies the twiddle of pass p + 1 to each output,
+// splits it and writes it straight into the A row of the group that takes it
+// in pass p + 1 (the Stockham exchange, without an FP32 buffer); after pass 2
+// thread t holds X[t + 256 j] and stores it with the post-chirp.  The A rows
+// of pass 1 are permuted (16 x 16 index transpose) so that these scattered
+// 4-byte stores meet at most 2 lanes per bank; thread t then owns group
+// transpose(t) in pass 1.
+//
+// Operand layout (umma_desc.h): K-major, no swizzle, core matrices of 8 rows
+// x 8 BF16 (16 bytes per row), LBO = 128 bytes along K, SBO = 512 bytes per 8
+// rows (32 K values per row).
+#include <cuda_bf16.h>
+
+#include "xft_engine.cuh"
+#include "xft_chirp.cuh"
+#include "xft_umma.cuh"
+
+namespace {
+
+using namespace xft;
+
+constexpr int kSL = 12, kSN = 1 << kSL, kST = 256;        // N, threads = groups
+constexpr uint32_t kPlane = 256 * 32 * 2;                  // one A plane: 256 rows x 32 BF16
+constexpr uint32_t kBPlane = 32 * 32 * 2;                  // one B plane
+constexpr uint32_t kOffAlo = kPlane, kOffBhi = 2 * kPlane, kOffBlo = 2 * kPlane + kBPlane;
+constexpr uint32_t kSmem = 2 * kPlane + 2 * kBPlane;       // 36 KB
+constexpr uint32_t kSLbo = 128, kSSbo = 512, kTmemCols = 64;
+constexpr uint64_t kSWaitNs = 2000000000ull;
+
+// Byte offset of element (row, k) of a 32-wide K-major BF16 operand.
+__host__ __device__ constexpr uint32_t boff(uint32_t r, uint32_t k) {
+    return (r >> 3) * kSSbo + (k >> 3) * kSLbo + (r & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ int transpose16(int g) { return ((g & 15) << 4) | (g >> 4); }
+
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unbf2(uint32_t v) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+    return __bfloat1622float2(h);
+}
+// hi = rn(re, im), lo = rn((re, im) - hi), each a BF16 pair (re low, im high)
+__device__ __forceinline__ void split_c(cpx<float> v, uint32_t& hi, uint32_t& lo) {
+    hi = bf2(v.x, v.y);
+    const float2 h = unbf2(hi);
+    lo = bf2(v.x - h.x, v.y - h.y);
+}
+
+__constant__ float kCosT16[16] = {
+    1.0f, 0.92387953251128676f, 0.70710678118654752f, 0.38268343236508977f,
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128676f,
+    -1.0f, -0.92387953251128676f, -0.70710678118654752f, -0.38268343236508977f,
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128676f};
+
+__device__ __forceinline__ bool bar_wait_all(uint64_t* bar, uint32_t parity) {
+    return xasync::mbar_wait(bar, parity, kSWaitNs);
+}
+
+__global__ void __launch_bounds__(kST, 3)
+k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
+                 const lct_desc* __restrict__ desc, int desc_step, int64_t count,
+                 const cpx<float>* __restrict__ tw, int32_t* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) umma::tmem_alloc(&tmem_slot, kTmemCols);
+    if (t == 0) {
+        xasync::mbar_init(&bar, 1);
+        xasync::fence_mbar_init();
+    }
+    // the DFT matrix, split: thread t writes 4 entries of B (row n = output
+    // index 2j + c', column k = input index 2e + c)
+    for (int q = t; q < 32 * 32; q += kST) {
+        const int n = q >> 5, k = q & 31;
+        const int j = n >> 1, cp = n & 1, e = k >> 1, c = k & 1;
+        const int m = (j * e) & 15;
+        const float re = kCosT16[m], im = -kCosT16[(m + 12) & 15];      // F_je = re + i im
+        const float v = cp == 0 ? (c == 0 ? re : -im) : (c == 0 ? im : re);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16*>(sm + kOffBhi + boff(n, k)) = h;
+        *reinterpret_cast<__nv_bfloat16*>(sm + kOffBlo + boff(n, k)) = l;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    // this thread's accumulator row: tile warp >> 2 (columns 32 tile ..), lane t
+    const uint32_t my_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+    constexpr uint32_t idesc = umma::instr_desc(umma::kFmtBF16, umma::kFmtBF16, 128, 32);
+    const uint32_t a_base = xasync::smem_addr(sm);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int64_t sig = blockIdx.x; sig < count && ok; sig += gridDim.x) {
+        const lct_desc D = desc[desc_step ? sig : 0];
+        const int64_t base = desc_step ? D.offset : sig * (int64_t)kSN;
+        const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
+        // pass 0 input: samples t + 256 e with the pre-chirp, into A row t
+        {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int n = t + kST * e;
+                const cpx<float> f = ld_stream(in + base + n);
+                split_c(cmul(f, pre_w<kSL, float>(D, n, decay)), hi[e], lo[e]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                *reinterpret_cast<uint4*>(sm + boff(t, 8 * q)) =
+                    make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+                *reinterpret_cast<uint4*>(sm + kOffAlo + boff(t, 8 * q)) =
+                    make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+            }
+        }
+#pragma unroll 1
+        for (int p = 0; p < 3; ++p) {
+            xasync::fence_proxy_async_smem();
+            umma::fence_before_sync();
+            __syncthreads();
+            if (t == 0) {
+                umma::fence_after_sync();
+#pragma unroll
+                for (int tile = 0; tile < 2; ++tile) {
+                    const uint32_t d = tmem + 32 * tile;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t o = tile * (16 * kSSbo) + ks * 2 * kSLbo;
+                        const uint64_t ah = umma::smem_desc(a_base + o, kSLbo, kSSbo);
+                        const uint64_t al = umma::smem_desc(a_base + kOffAlo + o, kSLbo, kSSbo);
+                        const uint64_t bh = umma::smem_desc(a_base + kOffBhi + ks * 2 * kSLbo, kSLbo, kSSbo);
+                        const uint64_t bl = umma::smem_desc(a_base + kOffBlo + ks * 2 * kSLbo, kSLbo, kSSbo);
+                        umma::mma_f16(d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+                        umma::mma_f16(d, ah, bl, idesc, 1u);
+                        umma::mma_f16(d, al, bh, idesc, 1u);
+                    }
+                }
+                umma::commit(&bar);
+            }
+            if (!bar_wait_all(&bar, phase)) {
+                ok = false;
+                atomicCAS(status, LCT_DEV_OK, LCT_DEV_TIMEOUT);
+            }
+            phase ^= 1u;
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
+            umma::fence_after_sync();
+            float v[32];
+            umma::tmem_ld16(my_row, v);
+            umma::tmem_ld16(my_row + 16, v + 16);
+            umma::fence_before_sync();
+            if (p == 2) {
+                // thread t holds X[t + 256 j]: post-chirp, scale, store
+                const float sc = (float)D.scale;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = t + kST * j;
+                    const cpx<float> y = {v[2 * j], v[2 * j + 1]};
+                    out[base + n] = cscale(cmul(y, post_w<kSL, float>(D, n)), sc);
+                }
+                break;
+            }
+            // Stockham exchange into pass p + 1: output j of group g goes to
+            // position pos = (g - k) 16 + k + j NS_p (k = g mod NS_p), i.e.
+            // group pos mod 256, element pos / 256, twiddled by
+            // e^{-2 pi i e' k' / (16 NS_{p+1})} (table entry), k' = group mod NS_{p+1}
+            const int g = p == 0 ? t : transpose16(t);
+            const int ns = p == 0 ? 1 : 16, ns1 = p == 0 ? 16 : 256, tw_off = p == 0 ? 0 : 240;
+            const int k = g & (ns - 1);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int pos = (g - k) * 16 + k + j * ns;
+                const int g1 = pos & 255, e1 = pos >> 8;
+                cpx<float> y = {v[2 * j], v[2 * j + 1]};
+                if (e1 > 0) y = cmul(y, ld_tw<float>(tw + tw_off + (e1 - 1) * ns1 + (g1 & (ns1 - 1))));
+                uint32_t hi, lo;
+                split_c(y, hi, lo);
+                const int row = p == 0 ? transpose16(g1) : g1;
+                const uint32_t o = boff((uint32_t)row, (uint32_t)(2 * e1));
+                *reinterpret_cast<uint32_t*>(sm + o) = hi;
+                *reinterpret_cast<uint32_t*>(sm + kOffAlo + o) = lo;
+            }
+        }
+    }
+    // every MMA issued has been waited on (or the wait gave up and the CTA
+    // stops); release the tensor memory
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+bool lct_split_umma_supported(int dtype, int log2n) { return dtype == 0 && log2n == kSL; }
+
+cudaError_t lct_launch_split_umma(int log2n, const void* in, void* out, const lct_desc* desc,
+                                  int desc_step, int64_t count, const void* tw, int32_t* status,
+                                  cudaStream_t stream) {
+    if (log2n != kSL || !tw) return cudaErrorInvalidValue;
+    static int blocks_per_sm[64] = {}, sms[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!blocks_per_sm[dev]) {
+        e = cudaFuncSetAttribute(k_xft_split_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmem);
+        if (e != cudaSuccess) return e;
+        // resident CTAs per SM from the kernel's own registers and shared
+        // memory (and 8 by tensor memory: 64 of 512 columns each); more CTAs
+        // than fit only wait for a slot, as the CTAs never wait on each other
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, k_xft_split_umma)) != cudaSuccess) return e;
+        int regs_sm = 0, smem_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+            return e;
+        const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 1) * kST);
+        const int by_smem = smem_sm / (int)(kSmem + fa.sharedSizeBytes + 1024);
+        int nb = by_regs < by_smem ? by_regs : by_smem;
+        nb = nb < 1 ? 1 : (nb > 8 ? 8 : nb);
+        blocks_per_sm[dev] = nb;
+    }
+    if (count <= 0) return cudaSuccess;
+    int64_t grid = (int64_t)blocks_per_sm[dev] * sms[dev];
+    if (grid > count) grid = count;
+    k_xft_split_umma<<<(unsigned)grid, kST, kSmem, stream>>>(
+        (const cpx<float>*)in, (cpx<float>*)out, desc, desc_step, count, (const cpx<float>*)tw, status);
+    return cudaGetLastError();
+}

@@ -167,3 +167,40 @@ def test_full_size_16384x4096(mode):
     err = rel_l2(G[idx], ref)
     print("%s full-size rel L2: max %.3e median %.3e" % (mode, err.max(), np.median(err)))
     assert err.max() < tol
+
+
+def test_tcgen05_split_bf16_n4096_complex_z_and_gapped_offsets():
+    """Split BF16 at N = 4096 runs on the tcgen05 tensor cores: a complex-z
+    fractional transform (decaying pre-chirp) and a batch plan with gaps
+    between the signals (offsets not multiples of N), against the oracle."""
+    N, count = 4096, 21
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=29, dtype=np.complex64)
+    z = 0.7 * np.exp(-2.2j)
+    abcd = O.abcd_of_z(z)
+    p = lct.Plan.create(N, *[complex(v) for v in abcd], dtype=lct.LCT_C64)
+    p.set_precision(lct.LCT_PREC_SPLIT_BF16)
+    try:
+        G = run(p.handle, f)
+        assert lct.lct_device_status(p.handle) == 0
+    finally:
+        p.destroy()
+    assert rel_l2(G, O.lct(f.astype(np.complex128), abcd)).max() < 1e-5
+    offs = np.arange(count, dtype=np.int64) * (N + 6) + 2
+    buf = np.zeros(offs[-1] + N + 5, dtype=np.complex64)
+    for s in range(count):
+        buf[offs[s]:offs[s] + N] = f[s]
+    p = lct.Plan.batch([N] * count, params, offs, dtype=lct.LCT_C64)
+    p.set_precision(lct.LCT_PREC_SPLIT_BF16)
+    try:
+        xin = torch.from_numpy(buf).cuda()
+        out = torch.zeros_like(xin)
+        lct.lct_execute(p.handle, xin, out, count)
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        Gb = out.cpu().numpy()
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(np.complex128), params)
+    for s in range(count):
+        assert rel_l2(Gb[offs[s]:offs[s] + N], ref[s]) < 1e-5
