@@ -154,7 +154,13 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     pre-chirp and inter-pass twiddles, then row DFTs with the post-chirp)
  *     in one persistent launch whose intermediate stays in a small ring of
  *     workspace slots (tens of MiB, owned by the plan), so it need not reach
- *     HBM (both dtypes, N = 8192 .. 65536; the default for N >= 32768).
+ *     HBM (both dtypes, N = 8192 .. 65536; the default for N >= 32768);
+ *  8  persistent CTAs whose input groups arrive by TMA tiled copies
+ *     (cp.async.bulk.tensor) through a tensor map that views the batch as
+ *     rows of 256 samples, one box per group of signals, completing on an
+ *     mbarrier while the previous group is transformed (complex64, N = 256
+ *     .. 8192, contiguous signals, 16-byte aligned input, batch N a multiple
+ *     of 256; other launches fall back to variant 0).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 /* The variant set on the plan, else the default for its N (7 for N >= 32768,

@@ -93,6 +93,16 @@ bool tma_ok(lct_plan p, const void* in) {
     return lct_fused_tma_supported(p->dtype, p->desc[0].log2n) && tma_aligned(p, in);
 }
 
+// Can variant 8 (tensor-map staged loads) run this launch: contiguous
+// signals addressed from `in` itself (the plan's own descriptors), 16-byte
+// aligned, whole 256-sample rows?
+bool tmat_ok(lct_plan p, const void* in, int64_t batch) {
+    const int log2n = p->desc[0].log2n;
+    return lct_fused_tmat_supported(p->dtype, log2n) && ((uintptr_t)in) % 16 == 0 &&
+           p->own_desc && (!p->is_batch || p->contiguous) &&
+           ((batch << log2n) % 256) == 0;
+}
+
 // Variant used when neither the plan nor the tune cache chooses one.
 int default_variant(lct_dtype dtype, int log2n) {
     return (lct_twopass_supported(dtype, log2n) && log2n >= kTwoPassDefaultLog2) ? 7 : 0;
@@ -180,6 +190,9 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
         return from_cuda(lct_launch_fused_pair(p->dtype, log2n, in, out, p->d_desc, desc_step,
                                                batch, tw2, stream));
     }
+    if (variant == 8 && tmat_ok(p, in, batch))
+        return from_cuda(lct_launch_fused_tmat(log2n, in, out, p->d_desc, desc_step, batch, tw,
+                                               p->d_status, stream));
     if ((variant == 1 || variant == 2) && tma_ok(p, in))
         return from_cuda(lct_launch_fused_tma(p->dtype, log2n, in, out, p->d_desc, desc_step,
                                               batch, tw, p->d_status, variant == 2, stream));
@@ -340,6 +353,7 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
         lct_desc* saved;
         ~swap() { p->d_desc = saved; }
     } restore{plan, plan->d_desc};
+    plan->own_desc = desc == plan->d_desc;
     plan->d_desc = const_cast<lct_desc*>(desc);
     const int desc_step = plan->is_batch ? 1 : 0;
     const lct_desc& D0 = plan->desc[0];
@@ -442,7 +456,7 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         return LCT_OK;
     }
     const int saved = plan->variant;
-    int candidates[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int candidates[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int n_cand = 1;
     if (lct_fused_pair8_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 6;
     if (lct_cluster_local_log2(plan->dtype, plan->desc[0].log2n) >= 0 &&
@@ -455,6 +469,8 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         candidates[n_cand++] = 1;
         candidates[n_cand++] = 2;
     }
+    plan->own_desc = true;
+    if (tmat_ok(plan, in, batch)) candidates[n_cand++] = 8;
     if (n_cand == 1) {
         plan->variant = 0;
         return LCT_OK;

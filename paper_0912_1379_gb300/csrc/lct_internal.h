@@ -108,6 +108,15 @@ cudaError_t lct_launch_fused_tma(int dtype, int log2n, const void* in, void* out
                                  cudaStream_t stream);
 bool lct_fused_tma_supported(int dtype, int log2n);
 
+// Variant 8: the persistent fused kernel with its input staged by TMA tiled
+// copies through a tensor map (complex64, N = 256 .. 8192, signal s at
+// element s N of `in`, count N a multiple of 256, 16-byte aligned `in`;
+// cudaErrorInvalidValue otherwise).
+bool lct_fused_tmat_supported(int dtype, int log2n);
+cudaError_t lct_launch_fused_tmat(int log2n, const void* in, void* out, const lct_desc* desc,
+                                  int desc_step, int64_t count, const void* tw, int32_t* status,
+                                  cudaStream_t stream);
+
 // Paired variant (complex64, N = 32 .. 8192): two signals per thread in
 // packed f32x2 registers.  tw_pair: lct_twiddle_table_pair(log2n).
 cudaError_t lct_launch_fused_pair(int dtype, int log2n, const void* in, void* out,

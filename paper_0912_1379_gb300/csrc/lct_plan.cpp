@@ -383,7 +383,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 7) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 8) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }

@@ -83,6 +83,9 @@ struct lct_plan_s {
     // starts when `in` is 16-byte aligned) and offset[s] == s N0
     bool even_offsets = true;
     bool contiguous = true;
+    // set by execute_locked: the launch reads the plan's own descriptor array
+    // (not a shifted sub-range of it, as chunked host-buffer execution passes)
+    bool own_desc = true;
 };
 
 namespace lcth {
@@ -117,6 +120,7 @@ int effective_variant(lct_plan p);
 bool tma_aligned(lct_plan p, const void* in);
 bool pair_tma_ok(lct_plan p, const void* in);
 bool tma_ok(lct_plan p, const void* in);
+bool tmat_ok(lct_plan p, const void* in, int64_t batch);
 lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, void* out,
                           int64_t batch, cudaStream_t stream);
 lct_status debug_check(lct_plan plan, const void* out, int64_t count, cudaStream_t stream);

@@ -105,7 +105,7 @@ def test_uniform_batch_per_signal_params(N, count, seed):
 
 
 @pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30), (16384, 9)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_kernel_variants(N, count, variant):
     """Both fused variants (one CTA per group / persistent with bulk-async
     prefetch) on per-signal parameters, with a ragged last group."""
@@ -120,6 +120,35 @@ def test_kernel_variants(N, count, variant):
     idx = np.unique(np.linspace(0, count - 1, n_check).astype(int))
     ref = O.lct(f[idx].astype(np.complex128), params[idx])
     assert rel_l2(G[idx], ref).max() < TOL32
+
+
+@pytest.mark.parametrize("N,count", [(256, 40), (256, 33), (4096, 7)])
+def test_tensor_map_variant_partial_groups_and_fallback(N, count):
+    """Variant 8 (TMA tensor-map staged loads): a last group that ends
+    inside its box (count not a multiple of the signals per CTA, zero-filled
+    rows), and a batch whose N count is not a multiple of 256 rows of the
+    tensor view (33 x 256 is, 7 x 4096 is; the gapped plan falls back)."""
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=N + 8 * count, dtype=np.complex64)
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N).set_variant(8)
+    try:
+        G = run(p.handle, f, np.complex64)
+    finally:
+        p.destroy()
+    ref = O.lct(f.astype(np.complex128), params)
+    assert rel_l2(G, ref).max() < TOL32
+    # gapped offsets: not contiguous, so the plan runs variant 0 instead
+    offs = np.arange(count, dtype=np.int64) * (N + 2)
+    buf = np.zeros(offs[-1] + N, dtype=np.complex64)
+    for s in range(count):
+        buf[offs[s]:offs[s] + N] = f[s]
+    p = lct.Plan.batch([N] * count, params, offs).set_variant(8)
+    try:
+        Gb = run(p.handle, buf[None, :], np.complex64, batch=count)[0]
+    finally:
+        p.destroy()
+    for s in range(count):
+        assert rel_l2(Gb[offs[s]:offs[s] + N], ref[s]) < TOL32
 
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
@@ -184,7 +213,7 @@ def test_autotune_picks_a_valid_variant():
         xin = to_dev(f, np.complex64)
         out = torch.empty_like(xin)
         v = p.autotune(xin, out, count)
-        assert v in (0, 1, 2, 3, 4, 5, 6)
+        assert v in (0, 1, 2, 3, 4, 5, 6, 8)
         G = run(p.handle, f, np.complex64)
     finally:
         p.destroy()
