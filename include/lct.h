@@ -282,6 +282,16 @@ lct_status lct2d_backward(lct2d_plan plan, const void* grad_out, const void* in,
                           int64_t batch, lct_stream_t stream);
 lct_status lct2d_plan_destroy(lct2d_plan plan);
 
+/* No counterpart in the paper: the data movement of a separable 2-D
+ * transform of one field sharded over several GPUs (rows on each GPU, an
+ * all-to-all exchange, then the columns as rows; see the Python binding's
+ * lct2d_sharded).  Transposes `batch` arrays of rows x cols vectors of `vec`
+ * complex samples: in [batch][rows][cols][vec] -> out [batch][cols][rows][vec]
+ * (device memory, dtype as lct_execute, in != out, else LCT_ERR_ARG; empty
+ * sizes are a no-op).  Asynchronous on `stream`. */
+lct_status lct_transpose(lct_dtype dtype, const void* in, void* out, int64_t rows, int64_t cols,
+                         int64_t vec, int64_t batch, lct_stream_t stream);
+
 /* Output points and rho of signal `index` of the plan (0 for single plans):
  * y_reim receives N complex points (2N doubles), rho N doubles (may be
  * NULL).  Host-only. */

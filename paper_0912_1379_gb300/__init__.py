@@ -72,6 +72,7 @@ def _load():
             "frft_hermite_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "frft_hermite_basis": [i64, dp, dp],
             "frft_hermite_status": [vp],
+            "lct_transpose": [i32, vp, vp, i64, i64, i64, i64, vp],
             "lct_output_grid": [vp, i64, dp, dp],
             "lct_input_grid": [i64, dp],
             "lct_plan_phase_turns": [vp, i64, up],
@@ -278,6 +279,13 @@ def frft_hermite_execute(N: int, z: complex, inp, out, batch: int, dtype: int = 
     z = complex(z)
     _check(_load().frft_hermite_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
                                         _stream_handle(stream)), "frft_hermite_execute")
+
+
+def lct_transpose(inp, out, rows: int, cols: int, vec: int = 1, batch: int = 1, dtype: int = LCT_C64,
+                  stream=None) -> None:
+    """[batch][rows][cols][vec] -> [batch][cols][rows][vec] on the device."""
+    _check(_load().lct_transpose(dtype, _ptr(inp), _ptr(out), rows, cols, vec, batch,
+                                 _stream_handle(stream)), "lct_transpose")
 
 
 def frft_hermite_status(stream=None) -> int:
@@ -531,3 +539,6 @@ def lct(x, abcd):
 def lct2d(x, abcd_x, abcd_y):
     """Differentiable separable 2-D LCT of x [..., ny, nx]."""
     return _fns()[1].apply(x, abcd_x, abcd_y)
+
+
+from .sharded import lct2d_sharded  # noqa: E402,F401

@@ -214,3 +214,19 @@ lct_status lct2d_plan_destroy(lct2d_plan plan) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// transposes for the multi-GPU separable 2-D transform
+// ---------------------------------------------------------------------------
+extern "C" lct_status lct_transpose(lct_dtype dtype, const void* in, void* out, int64_t rows,
+                                    int64_t cols, int64_t vec, int64_t batch, lct_stream_t stream) {
+    if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
+    if (rows < 0 || cols < 0 || vec < 1 || batch < 0) return LCT_ERR_ARG;
+    if (rows == 0 || cols == 0 || batch == 0) return LCT_OK;
+    if (in == out) return LCT_ERR_ARG;
+    lct_status st = check_ptr(in, dtype);
+    if (st == LCT_OK) st = check_ptr(out, dtype);
+    if (st != LCT_OK) return st;
+    return from_cuda(lct_launch_transpose((int)dtype, in, out, rows, cols, vec, batch,
+                                          (cudaStream_t)stream));
+}

@@ -255,6 +255,11 @@ cudaError_t lct_launch_plain_pre(int dtype, int log2n, const void* in, void* wor
 cudaError_t lct_launch_plain_post(int dtype, int log2n, const void* work, void* out,
                                   const lct_desc* desc, int desc_step, int64_t count,
                                   cudaStream_t stream);
+// Batched transpose (k_transpose.cu): in [batch][rows][cols][vec] ->
+// out [batch][cols][rows][vec], complex samples of the dtype.
+cudaError_t lct_launch_transpose(int dtype, const void* in, void* out, int64_t rows, int64_t cols,
+                                 int64_t vec, int64_t batch, cudaStream_t stream);
+
 // Plain FP32 baseline pieces (complex64 in/out).  work: complex64 [count][N].
 cudaError_t lct_launch_plain32_pre(const void* in, void* work, const lct_desc* desc, int log2n,
                                    int desc_step, int64_t count, cudaStream_t stream);

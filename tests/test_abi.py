@@ -119,9 +119,12 @@ def test_variant_selection_host_only():
         assert lct.lct_plan_get_variant(p) == 1
         lct.lct_plan_set_variant(p, 7)
         assert lct.lct_plan_get_variant(p) == 7
-        with pytest.raises(lct.LctError) as e:
-            lct.lct_plan_set_variant(p, 8)
-        assert e.value.status == 1
+        lct.lct_plan_set_variant(p, 8)
+        assert lct.lct_plan_get_variant(p) == 8
+        for bad in (9, -1):
+            with pytest.raises(lct.LctError) as e:
+                lct.lct_plan_set_variant(p, bad)
+            assert e.value.status == 1
     finally:
         lct.lct_plan_destroy(p)
     # default: two passes from N = 32768 up, else variant 0

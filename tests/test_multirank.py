@@ -142,3 +142,85 @@ def test_partition_properties():
         lct.lct_partition(np.array([70000]), 2)          # above 65536
     with pytest.raises(lct.LctError):
         lct.lct_partition(Ns, 0)
+
+
+# --------------------------------------------------------------------------
+# one 2-D field sharded over two ranks: rows, all-to-all, columns
+# --------------------------------------------------------------------------
+def _field(ny, nx, seed=7):
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    y, x = O.nodes(ny), O.nodes(nx)
+    env = np.exp(-(y[:, None] ** 2 + x[None, :] ** 2) / 18.0)
+    return env * (rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx)))
+
+
+AX = (0.6, 1.3, (0.6 * -0.4 - 1) / 1.3, -0.4)
+AY = (-1.1, -0.7, (-1.1 * 0.9 - 1) / -0.7, 0.9)
+
+
+def _cpu_rows(x, abcd):
+    """Stand-in for the GPU row transform on a CPU rank: the FP64 oracle."""
+    import oracle as O
+    return torch.from_numpy(O.lct(x.numpy(), abcd))
+
+
+def _cpu_transpose(x, rows, cols, vec):
+    """Stand-in for lct_transpose on a CPU rank (same memory contract)."""
+    a = x.numpy().reshape(rows, cols, vec).transpose(1, 0, 2)
+    return torch.from_numpy(np.ascontiguousarray(a).reshape(x.shape))
+
+
+def _sharded_worker(rank, port, errq):
+    try:
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
+        os.environ["MASTER_PORT"] = str(port)
+        dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+        import oracle as O
+        from paper_0912_1379_gb300.sharded import lct2d_sharded
+        ny, nx = 64, 128
+        f = _field(ny, nx)
+        R, C = ny // WORLD, nx // WORLD
+        mine = torch.from_numpy(np.ascontiguousarray(f[rank * R:(rank + 1) * R]))
+        out = lct2d_sharded(mine, AX, AY, row_transform=_cpu_rows, transpose=_cpu_transpose)
+        assert tuple(out.shape) == (C, ny)
+        parts = [torch.zeros_like(torch.view_as_real(out)) for _ in range(WORLD)]
+        dist.all_gather(parts, torch.view_as_real(out.contiguous()))
+        if rank == 0:
+            got = np.concatenate([torch.view_as_complex(p).numpy() for p in parts])   # [nx][ny]
+            rows = O.lct(f, AX)                     # 1-D transform of every row (along x)
+            ref = O.lct(np.ascontiguousarray(rows.T), AY)   # then every column (along y), transposed
+            err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert err < 1e-13, err
+        dist.barrier()
+        dist.destroy_process_group()
+    except Exception:
+        errq.put((rank, traceback.format_exc()))
+        raise
+
+
+def test_two_ranks_sharded_2d_field():
+    """The exchange of lct2d_sharded (row transform, transpose, all-to-all,
+    transpose, column transform) on two gloo ranks, with the oracle and a
+    host transpose standing in for each rank's GPU kernels; the gathered
+    result equals the oracle's separable 2-D transform of the whole field."""
+    import oracle as O
+    import paper_0912_1379_gb300 as lct
+    lct.build()
+    O.build()
+    ctx = mp.get_context("spawn")
+    errq = ctx.SimpleQueue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, port, errq)) for r in range(WORLD)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    errors = []
+    while not errq.empty():
+        errors.append(errq.get())
+    assert not errors, errors
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
