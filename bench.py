@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8", "9"],
                     help="fused kernel variant (auto: the library's autotuner)")
     ap.add_argument("--precision", default="native",
                     choices=["native", "split_bf16", "split_fp16", "fp16"],
@@ -366,8 +366,11 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
             k = pos[s]
             buf[offs[k]:offs[k] + Ns[s]] = sig
     plan = lct.Plan.batch(Ns[mine], abcd[mine], offs, dtype=lct.LCT_C64)
+    persistent = args.variant == "9"
+    if persistent:
+        plan.set_variant(9)              # one persistent launch over a work queue
     # one kernel per (N, kind) group in the graph (b = 0 signals form their own groups)
-    n_groups = len({(int(Ns[s]), bool(abcd[s][1] == 0)) for s in mine})
+    n_groups = 1 if persistent else len({(int(Ns[s]), bool(abcd[s][1] == 0)) for s in mine})
     d_in = torch.from_numpy(buf).cuda()
     d_out = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()
@@ -434,10 +437,13 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
                        "points": total, "signals_by_N": by_n,
                        "sharding": "lct_partition over %d ranks (cost N log2 N, largest first); "
                                    "load imbalance %.2e" % (world, load.max() / load.mean() - 1),
-                       "l2": "inputs larger than L2 (1.9 GB per buffer at one GPU), no flush"},
+                       "l2": "inputs larger than L2 (1.9 GB per buffer at one GPU), no flush",
+                       "launch": "one persistent kernel over a largest-first work queue" if persistent
+                                 else "CUDA graph: one kernel per N group + one b = 0 launch"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "whole graph (one kernel per N group + b = 0 chunks), 16 B/point"},
+                         "kernel": ("k_xft_ragged (persistent, all items)" if persistent else
+                                    "whole graph (one kernel per N group + b = 0 chunks)") + ", 16 B/point"},
             "accuracy": accuracy,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -160,7 +160,12 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     rows of 256 samples, one box per group of signals, completing on an
  *     mbarrier while the previous group is transformed (complex64, N = 256
  *     .. 8192, contiguous signals, 16-byte aligned input, batch N a multiple
- *     of 256; other launches fall back to variant 0).
+ *     of 256; other launches fall back to variant 0);
+ *  9  ragged batch plans (complex64, powers of two): the whole batch in one
+ *     persistent launch that takes work items from one device queue,
+ *     largest N first -- the two-pass tiles of every N >= 8192, then groups
+ *     of signals of N <= 4096, then the b = 0 chunks -- instead of the CUDA
+ *     graph of one kernel per N (other ragged plans keep the graph).
  * LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
 /* The variant set on the plan, else the default for its N (7 for N >= 32768,

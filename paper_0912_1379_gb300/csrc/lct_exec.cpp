@@ -330,8 +330,87 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
     return LCT_OK;
 }
 
+// Persistent ragged launch (variant 9, complex64 plans of power-of-two N):
+// the work queue, largest N first -- the two-pass tiles of each group of
+// N >= 8192, then the fused items of N <= 4096, then the b = 0 chunks.
+bool ragged_persistent_ok(lct_plan p) {
+    if (p->dtype != LCT_C64) return false;
+    for (const auto& g : p->groups)
+        if (g.kind != LCT_KIND_DIAG && !(g.kind == LCT_KIND_XFT && g.log2n >= 1 && g.log2n <= 16))
+            return false;
+    return true;
+}
+
+lct_status build_ragged_persistent(lct_plan p) {
+    std::vector<int4> items;
+    std::vector<lct_rg_group> tg;
+    int64_t work = 0, sync = 0;
+    for (const auto& g : p->groups) {
+        if (g.kind == LCT_KIND_DIAG) {
+            for (int64_t c = 0; c < g.nchunks; ++c)
+                items.push_back(make_int4(LCT_RG_DIAG, (int)(g.chunk_off + c), (int)g.idx_off, 0));
+            continue;
+        }
+        if (g.log2n >= 13) {
+            int64_t slots = 0;
+            if (lct_twopass_ring(0, g.log2n, g.count, &slots) != cudaSuccess || slots < 3)
+                return LCT_ERR_CUDA;
+            int cb = 0, rb = 0;
+            lct_twopass_tiles(g.log2n, &cb, &rb);
+            lct_rg_group r;
+            r.count = g.count;
+            r.slots = slots;
+            r.lag = slots - 2;
+            r.idx_off = g.idx_off;
+            r.work_off = work;
+            r.sync_off = sync;
+            r.log2n = g.log2n;
+            r.pad = 0;
+            work += slots << g.log2n;
+            sync += 4 + 2 * slots;
+            const int gi = (int)tg.size();
+            tg.push_back(r);
+            const int64_t total = g.count * (cb + rb);
+            for (int64_t q = 0; q < total; ++q)
+                items.push_back(make_int4(LCT_RG_TP, gi, (int)(uint32_t)(q >> 32), (int)(uint32_t)q));
+            continue;
+        }
+        const int spc = lct_ragged_fused_spc(g.log2n);
+        for (int64_t j = 0; j < g.count; j += spc)
+            items.push_back(make_int4(LCT_RG_FUSED, g.log2n, (int)(g.idx_off + j),
+                                      (int)(g.count - j < spc ? g.count - j : spc)));
+    }
+    for (int l = 5; l <= 12; ++l) {
+        p->rg_tw[l] = lct_twiddle_table(LCT_C64, l);
+        if (!p->rg_tw[l]) return LCT_ERR_OOM;
+    }
+    const size_t ib = items.size() * sizeof(int4), gb = (tg.empty() ? 1 : tg.size()) * sizeof(lct_rg_group);
+    p->rg_sync_bytes = (size_t)(2 + sync) * sizeof(int32_t);
+    if (cudaMalloc(&p->d_rg_items, ib ? ib : sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&p->d_rg_groups, gb) != cudaSuccess ||
+        cudaMalloc(&p->d_rg_work, (size_t)(work ? work : 1) * sample_bytes(p->dtype)) != cudaSuccess ||
+        cudaMalloc(&p->d_rg_sync, p->rg_sync_bytes) != cudaSuccess)
+        return LCT_ERR_OOM;
+    if ((ib && cudaMemcpy(p->d_rg_items, items.data(), ib, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!tg.empty() && cudaMemcpy(p->d_rg_groups, tg.data(), tg.size() * sizeof(lct_rg_group),
+                                   cudaMemcpyHostToDevice) != cudaSuccess))
+        return LCT_ERR_CUDA;
+    p->rg_items = (int64_t)items.size();
+    return LCT_OK;
+}
+
 lct_status run_ragged(lct_plan p, const void* in, void* out, cudaStream_t stream) {
     if (p->prec != LCT_PREC_NATIVE) return LCT_ERR_UNSUPPORTED;
+    if (p->variant == 9 && ragged_persistent_ok(p)) {
+        if (!p->d_rg_items) {
+            lct_status st = build_ragged_persistent(p);
+            if (st != LCT_OK) return st;
+        }
+        return from_cuda(lct_launch_ragged(in, out, p->d_desc, p->d_idx, p->d_rg_items, p->rg_items,
+                                           p->d_rg_groups, (const int4*)p->d_chunks, p->d_rg_work,
+                                           p->d_rg_sync, p->rg_sync_bytes, p->rg_tw, p->d_status,
+                                           stream));
+    }
     if (!p->gexec || p->g_in != in || p->g_out != out) {
         lct_status st = build_graph(p, in, out);
         if (st != LCT_OK) return st;

@@ -152,6 +152,27 @@ cudaError_t lct_launch_twopass(int dtype, int log2n, const void* in, void* out, 
                                const int32_t* idx, int32_t* status, const void* tw1,
                                const void* tw2, cudaStream_t stream);
 
+// Persistent ragged kernel (k_ragged.cu, complex64): one launch over a work
+// queue of int4 items -- {LCT_RG_TP, group, p >> 32, p & 0xffffffff}: tile p
+// of the two-pass group; {LCT_RG_FUSED, log2n, position in idx, count}: up
+// to lct_ragged_fused_spc(log2n) signals of N <= 4096; {LCT_RG_DIAG, chunk
+// index, position of the b = 0 index list, 0}.  groups: the two-pass groups
+// (ring workspace at work + work_off samples, counters at sync + 2 +
+// sync_off int32); sync: the queue word (2 int32) then the counters, zeroed
+// by the launch (sync_bytes in all); tw[L]: lct_twiddle_table(0, L).
+enum { LCT_RG_TP = 0, LCT_RG_FUSED = 1, LCT_RG_DIAG = 2 };
+struct lct_rg_group {
+    int64_t count, lag, slots, idx_off, work_off, sync_off;
+    int32_t log2n, pad;
+};
+void lct_twopass_tiles(int log2n, int* cb, int* rb);
+int lct_ragged_fused_spc(int log2n);
+size_t lct_ragged_smem_bytes();
+cudaError_t lct_launch_ragged(const void* in, void* out, const lct_desc* desc, const int32_t* idx,
+                              const int4* items, int64_t n_items, const lct_rg_group* groups,
+                              const int4* chunks, void* work, int32_t* sync, size_t sync_bytes,
+                              const void* const* tw, int32_t* status, cudaStream_t stream);
+
 // Self-test of the bounded waits (k_selftest.cu): word[0..2] zeroed device
 // int32; which 0 = mbarrier wait, 1 = counter wait.
 cudaError_t lct_launch_selftest_wait(int which, uint64_t limit_ns, int32_t* word,

@@ -135,6 +135,16 @@ void release_device(lct_plan p) {
     p->d_idx = nullptr;
     cudaFree(p->d_chunks);
     p->d_chunks = nullptr;
+    cudaFree(p->d_rg_items);
+    cudaFree(p->d_rg_groups);
+    cudaFree(p->d_rg_work);
+    cudaFree(p->d_rg_sync);
+    p->d_rg_items = nullptr;
+    p->d_rg_groups = nullptr;
+    p->d_rg_work = nullptr;
+    p->d_rg_sync = nullptr;
+    p->rg_items = 0;
+    p->rg_sync_bytes = 0;
     cudaFree(p->d_coef);
     cudaFree(p->d_partial);
     p->d_coef = nullptr;
@@ -383,7 +393,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 8) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 9) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }

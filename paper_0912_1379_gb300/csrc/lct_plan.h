@@ -66,6 +66,15 @@ struct lct_plan_s {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kBranches] = {};
     cudaGraphExec_t gexec = nullptr;
+    // persistent ragged launch (variant 9): its work queue, two-pass group
+    // table, ring workspace and counters, built on first use
+    int4* d_rg_items = nullptr;
+    lct_rg_group* d_rg_groups = nullptr;
+    int64_t rg_items = 0;
+    void* d_rg_work = nullptr;
+    int32_t* d_rg_sync = nullptr;
+    size_t rg_sync_bytes = 0;
+    const void* rg_tw[17] = {};
     // host-buffer execution: copy-in, compute and copy-out streams, two
     // staging buffer pairs of `hx_chunk` signals, and their events
     cudaStream_t hx_stream[3] = {};

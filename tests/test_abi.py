@@ -121,7 +121,7 @@ def test_variant_selection_host_only():
         assert lct.lct_plan_get_variant(p) == 7
         lct.lct_plan_set_variant(p, 8)
         assert lct.lct_plan_get_variant(p) == 8
-        for bad in (9, -1):
+        for bad in (10, -1):
             with pytest.raises(lct.LctError) as e:
                 lct.lct_plan_set_variant(p, bad)
             assert e.value.status == 1

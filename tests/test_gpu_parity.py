@@ -520,9 +520,14 @@ RAGGED_SPECS = [
 ]
 
 
-def test_ragged_mixed_sizes_and_kinds():
+@pytest.mark.parametrize("variant", [None, 9])
+def test_ragged_mixed_sizes_and_kinds(variant):
+    """variant None: the CUDA graph of one kernel per N; 9: one persistent
+    launch over a largest-first work queue."""
     Ns, abcds, offs, buf, sigs = _ragged_case(RAGGED_SPECS, seed=31)
     p = lct.Plan.batch(Ns, abcds, offs, dtype=lct.LCT_C64)
+    if variant is not None:
+        p.set_variant(variant)
     try:
         x = torch.from_numpy(buf).cuda()
         out = torch.zeros_like(x)
@@ -563,8 +568,9 @@ SMALL_SPECS = [
 ]
 
 
-@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
-def test_ragged_smallest_sizes_both_dtypes(dtype):
+@pytest.mark.parametrize("dtype,variant", [(np.complex64, None), (np.complex128, None),
+                                           (np.complex64, 9)])
+def test_ragged_smallest_sizes_both_dtypes(dtype, variant):
     """Ragged plans with N = 2 .. 32 (several signals per CTA), b = 0 signals
     below and above the 2048-sample chunk of the diagonal launch, and -- in
     complex128 -- an N = 32768 signal on the persistent two-pass kernel."""
@@ -574,6 +580,8 @@ def test_ragged_smallest_sizes_both_dtypes(dtype):
     Ns, abcds, offs, buf, sigs = _ragged_case(specs, seed=53)
     code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
     p = lct.Plan.batch(Ns, abcds, offs, dtype=code)
+    if variant is not None:
+        p.set_variant(variant)
     try:
         x = torch.from_numpy(buf.astype(dtype)).cuda()
         out = torch.zeros_like(x)
@@ -593,9 +601,11 @@ def test_ragged_smallest_sizes_both_dtypes(dtype):
     assert np.all(G[mask] == 0)
 
 
-def test_ragged_full_size_workload():
+@pytest.mark.parametrize("variant", [None, 9])
+def test_ragged_full_size_workload(variant):
     """The 20000-instance ragged workload (N = 2^6..2^16, four kinds), one
-    graph launch; parity on a sample of signals, Parseval on all real ones."""
+    graph launch (variant None) or one persistent launch (9); parity on a
+    sample of signals, Parseval on all real ones."""
     r = W.ragged_plan()
     M = len(r["kind"])
     Ns = (1 << r["log2n"]).astype(np.int64)
@@ -611,6 +621,8 @@ def test_ragged_full_size_workload():
         x = O.nodes(int(Ns[s]))
         buf[offs[s]:offs[s] + Ns[s]] = W.ragged_signal(x, r["s"][s], r["q"][s], rng)
     p = lct.Plan.batch(Ns, abcd, offs, dtype=lct.LCT_C64)
+    if variant is not None:
+        p.set_variant(variant)
     try:
         xin = torch.from_numpy(buf).cuda()
         out = torch.empty_like(xin)
