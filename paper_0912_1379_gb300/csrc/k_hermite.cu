@@ -263,6 +263,19 @@ __device__ __forceinline__ void umma_drain(uint32_t taddr, float* sum) {
     }
 }
 
+// The 8 complex inputs thread tid contributes to A chunk c: signal
+// b0 + tid / 4, inputs 32 c + 8 (tid & 3) + 0..7 (zero outside).
+__device__ __forceinline__ void load_a_chunk(const cpx<float>* __restrict__ A, int64_t batch, int n,
+                                             int64_t b0, int c, int tid, cpx<float>* pre) {
+    const int64_t b = b0 + (tid >> 2);
+    const int k0 = c * kUK + (tid & 3) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        pre[e] = (b < batch && k < n) ? A[b * n + k] : cpx<float>{0.f, 0.f};
+    }
+}
+
 __global__ void __launch_bounds__(kUThreads, 1)
 k_herm_umma(const cpx<float>* __restrict__ A, const float* __restrict__ Bblk,
             cpx<float>* __restrict__ C, const cpx<float>* __restrict__ alpha, int64_t batch, int n,
@@ -292,6 +305,16 @@ k_herm_umma(const cpx<float>* __restrict__ A, const float* __restrict__ Bblk,
     float sum[128];
 #pragma unroll
     for (int i = 0; i < 128; ++i) sum[i] = 0.f;
+    cpx<float> pre[8];                        // this thread's A values of the next chunk
+    load_a_chunk(A, batch, n, b0, 0, tid, pre);
+    if (tid == 0) {                           // B of chunks 0 and 1 into the two free stages
+        for (int c0 = 0; c0 < 2 && c0 < kc_count; ++c0) {
+            float* b1 = reinterpret_cast<float*>(sm + c0 * kUStage + 2 * kUASz);
+            xasync::mbar_arrive_expect_tx(&bar_b[c0], 2 * kUBSz);
+            xasync::bulk_g2s(b1, Bblk + ((int64_t)jt * kc_count + c0) * (2 * kUBSz / 4), 2 * kUBSz,
+                             &bar_b[c0]);
+        }
+    }
     bool ok = true;
     int c = 0;
     for (; c < kc_count; ++c) {
@@ -299,52 +322,39 @@ k_herm_umma(const cpx<float>* __restrict__ A, const float* __restrict__ Bblk,
         unsigned char* st = sm + s * kUStage;
         float* a_hi = reinterpret_cast<float*>(st);
         float* a_lo = reinterpret_cast<float*>(st + kUASz);
-        float* b_hi = reinterpret_cast<float*>(st + 2 * kUASz);
-        // chunk c - 2 (stage s, accumulator s) complete: drain it, then reuse
+        // chunk c - 2 (stage s, accumulator s) is complete -- thread 0 waited
+        // for it after issuing chunk c - 1, and issued chunk c's B copy --
+        // so drain its accumulator and reuse the stage
         if (c >= 2) {
-            if (tid == 0) ok = xasync::mbar_wait(&bar_mma[s], ((c - 2) >> 1) & 1, kUWaitNs);
             if (!__syncthreads_and(ok)) break;
             umma::fence_after_sync();
             umma_drain(my_acc + (uint32_t)(s * kUTmemCols), sum);
             umma::fence_before_sync();
         }
-        if (tid == 0) {
-            xasync::mbar_arrive_expect_tx(&bar_b[s], 2 * kUBSz);
-            xasync::bulk_g2s(b_hi, Bblk + ((int64_t)jt * kc_count + c) * (2 * kUBSz / 4), 2 * kUBSz,
-                             &bar_b[s]);
-        }
-        // A chunk: signal bb = tid / 4, inputs k = 32 c + 8 (tid & 3) + 0..7;
-        // row 2 bb holds the real parts, row 2 bb + 1 the imaginary parts
+        // A chunk c (loaded into registers one chunk ahead): signal bb =
+        // tid / 4, inputs k = 32 c + 8 (tid & 3) + 0..7; row 2 bb holds the
+        // real parts, row 2 bb + 1 the imaginary parts
         {
             const int bb = tid >> 2, kq = (tid & 3) * 8;
-            const int64_t b = b0 + bb;
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-                float re[4], im[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = c * kUK + kq + 4 * g + e;
-                    cpx<float> v = {0.f, 0.f};
-                    if (b < batch && k < n) v = A[b * n + k];
-                    re[e] = v.x;
-                    im[e] = v.y;
-                }
                 const uint32_t o_re = umma::tf32_offset(2 * bb, kq + 4 * g, kUK) / 4;
                 const uint32_t o_im = umma::tf32_offset(2 * bb + 1, kq + 4 * g, kUK) / 4;
                 float4 h, l;
-                h.x = umma::to_tf32(re[0]); l.x = umma::to_tf32(re[0] - h.x);
-                h.y = umma::to_tf32(re[1]); l.y = umma::to_tf32(re[1] - h.y);
-                h.z = umma::to_tf32(re[2]); l.z = umma::to_tf32(re[2] - h.z);
-                h.w = umma::to_tf32(re[3]); l.w = umma::to_tf32(re[3] - h.w);
+                h.x = umma::to_tf32(pre[4 * g + 0].x); l.x = umma::to_tf32(pre[4 * g + 0].x - h.x);
+                h.y = umma::to_tf32(pre[4 * g + 1].x); l.y = umma::to_tf32(pre[4 * g + 1].x - h.y);
+                h.z = umma::to_tf32(pre[4 * g + 2].x); l.z = umma::to_tf32(pre[4 * g + 2].x - h.z);
+                h.w = umma::to_tf32(pre[4 * g + 3].x); l.w = umma::to_tf32(pre[4 * g + 3].x - h.w);
                 *reinterpret_cast<float4*>(a_hi + o_re) = h;
                 *reinterpret_cast<float4*>(a_lo + o_re) = l;
-                h.x = umma::to_tf32(im[0]); l.x = umma::to_tf32(im[0] - h.x);
-                h.y = umma::to_tf32(im[1]); l.y = umma::to_tf32(im[1] - h.y);
-                h.z = umma::to_tf32(im[2]); l.z = umma::to_tf32(im[2] - h.z);
-                h.w = umma::to_tf32(im[3]); l.w = umma::to_tf32(im[3] - h.w);
+                h.x = umma::to_tf32(pre[4 * g + 0].y); l.x = umma::to_tf32(pre[4 * g + 0].y - h.x);
+                h.y = umma::to_tf32(pre[4 * g + 1].y); l.y = umma::to_tf32(pre[4 * g + 1].y - h.y);
+                h.z = umma::to_tf32(pre[4 * g + 2].y); l.z = umma::to_tf32(pre[4 * g + 2].y - h.z);
+                h.w = umma::to_tf32(pre[4 * g + 3].y); l.w = umma::to_tf32(pre[4 * g + 3].y - h.w);
                 *reinterpret_cast<float4*>(a_hi + o_im) = h;
                 *reinterpret_cast<float4*>(a_lo + o_im) = l;
             }
+            if (c + 1 < kc_count) load_a_chunk(A, batch, n, b0, c + 1, tid, pre);
         }
         xasync::fence_proxy_async_smem();
         __syncthreads();
@@ -371,6 +381,19 @@ k_herm_umma(const cpx<float>* __restrict__ A, const float* __restrict__ Bblk,
                     umma::mma_tf32(d, dal, dbh, idesc, 1u);
                 }
                 umma::commit(&bar_mma[s]);
+                // stage 1 - s is free once chunk c - 1 completes: wait for it
+                // and start chunk c + 1's B copy into that stage now
+                if (c + 1 < kc_count) {
+                    const int s1 = s ^ 1;
+                    if (c >= 1) ok = xasync::mbar_wait(&bar_mma[s1], ((c - 1) >> 1) & 1, kUWaitNs);
+                    if (ok && c >= 1) {
+                        float* b1 = reinterpret_cast<float*>(sm + s1 * kUStage + 2 * kUASz);
+                        xasync::mbar_arrive_expect_tx(&bar_b[s1], 2 * kUBSz);
+                        xasync::bulk_g2s(b1, Bblk + ((int64_t)jt * kc_count + c + 1) * (2 * kUBSz / 4),
+                                         2 * kUBSz, &bar_b[s1]);
+                    }
+                    if (!ok) record_umma_timeout();
+                }
             }
         }
         if (!__syncthreads_and(ok)) break;          // chunk c was not issued
