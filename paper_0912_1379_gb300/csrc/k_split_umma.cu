@@ -79,7 +79,7 @@ __device__ __forceinline__ bool bar_wait_all(uint64_t* bar, uint32_t parity) {
     return xasync::mbar_wait(bar, parity, kSWaitNs);
 }
 
-__global__ void __launch_bounds__(kST, 3)
+__global__ void __launch_bounds__(kST, 4)
 k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
                  const lct_desc* __restrict__ desc, int desc_step, int64_t count,
                  const cpx<float>* __restrict__ tw, int32_t* __restrict__ status) {
