@@ -65,6 +65,8 @@ def _load():
             lib.oracle_lct_grad_params.restype = ctypes.c_int
             lib.oracle_lct_matrix.argtypes = [i64, dp, dp]
             lib.oracle_lct_matrix.restype = ctypes.c_int
+            lib.oracle_frft_mehler.argtypes = [i64, i64, ctypes.c_double, ctypes.c_double, dp, dp]
+            lib.oracle_frft_mehler.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -208,3 +210,19 @@ def frft(f, z: complex, return_rho: bool = False):
     if return_rho:
         return res[0] * s, res[1]
     return res[0] * s
+
+
+def frft_mehler(f, z: complex) -> np.ndarray:
+    """F_z for complex z (|z| <= 1, z != +-1) on the real nodes y_j = x_j:
+    the matrix of eq. (fasy) times the samples, eq. (primcuad) -- the Riemann
+    sum of eq. (eqifft) that eq. (cuadtrfor) states.  Rows of f are signals."""
+    f_in = np.asarray(f)
+    fs = _signals(f)
+    count, N = fs.shape
+    z = complex(z)
+    g = np.empty_like(fs)
+    rc = _load().oracle_frft_mehler(N, count, z.real, z.imag, _dp(fs.view(np.float64)),
+                                    _dp(g.view(np.float64)))
+    if rc != 0:
+        raise ValueError("oracle_frft_mehler: |z| <= 1 and z != +-1 required")
+    return g.reshape(f_in.shape)

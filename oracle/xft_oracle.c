@@ -369,3 +369,79 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/*
+ * Fractional transform for complex z on the real nodes, Sec. 2: the matrix
+ * of eq. (fasy) (the large-N form of eq. (tmat) by Mehler's formula) applied
+ * to the samples f_k = f(x_k), eq. (primcuad), i.e. the Riemann sum of
+ * eq. (eqifft) at y_j = x_j (eq. (cuadtrfor)):
+ *
+ *   g_j = sqrt(2/(1 - z^2)) dx sum_k e^{E_jk} f_k,
+ *   E_jk = -[(1 + z^2)(x_j^2 + x_k^2) - 4 x_j x_k z] / (2 (1 - z^2)),
+ *
+ * for |z| <= 1, z != +-1 (the paper states |z| < 1; on the unit circle the
+ * same sum is the real-angle kernel).  With x_k = pi m_k / (2 sqrt(2N)),
+ *   x_j^2 + x_k^2 = pi^2 (m_j^2 + m_k^2) / (8N),  x_j x_k = pi^2 m_j m_k / (8N),
+ * integers formed exactly.  P = (1 + z^2) / (2 (1 - z^2)) and
+ * Q = 2 z / (1 - z^2) are formed in long double from the FP64 z, so that
+ *   E_jk = -P pi^2 (m_j^2 + m_k^2)/(8N) + Q pi^2 m_j m_k/(8N),
+ * and Im E is reduced modulo one turn in long double before its sine and
+ * cosine are taken.  f, g: count signals of N interleaved complex doubles.
+ * Returns -1 for |z| > 1 or z = +-1.
+ */
+int oracle_frft_mehler(int64_t N, int64_t count, double z_re, double z_im, const double* f,
+                       double* g) {
+    const ld zr = z_re, zi = z_im;
+    if (zr * zr + zi * zi > 1.0L + 1e-15L || (zi == 0.0L && fabsl(zr) == 1.0L)) return -1;
+    /* z^2, 1 + z^2, 1 - z^2 */
+    const ld z2r = zr * zr - zi * zi, z2i = 2.0L * zr * zi;
+    const ld pr = 1.0L + z2r, pi_ = z2i;          /* 1 + z^2 */
+    const ld mr = 1.0L - z2r, mi = -z2i;          /* 1 - z^2 */
+    const ld den = mr * mr + mi * mi;
+    /* P = (1 + z^2) / (2 (1 - z^2)),  Q = 2 z / (1 - z^2) */
+    const ld Pr = (pr * mr + pi_ * mi) / (2.0L * den), Pi = (pi_ * mr - pr * mi) / (2.0L * den);
+    const ld Qr = 2.0L * (zr * mr + zi * mi) / den, Qi = 2.0L * (zi * mr - zr * mi) / den;
+    const ld unit = PI_L * PI_L / (8.0L * (ld)N);
+    /* prefactor sqrt(2/(1 - z^2)) dx, principal root */
+    cplx two = {2.0, 0.0};
+    cplx omz2 = {(double)mr, (double)mi};
+    cplx pre = c_scale(c_sqrt(c_div(two, omz2)), (double)(PI_L / sqrtl(2.0L * (ld)N)));
+    const cplx* fc = (const cplx*)f;
+    cplx* gc = (cplx*)g;
+    int fail = 0;
+    #pragma omp parallel
+    {
+        cplx* row = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+        if (!row) {
+            #pragma omp atomic write
+            fail = 1;
+        }
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < N; ++j) {
+            if (!row) continue;
+            const int64_t mj = node_m(N, j);
+            for (int64_t k = 0; k < N; ++k) {
+                const int64_t mk = node_m(N, k);
+                const ld S = (ld)(mj * mj + mk * mk) * unit;
+                const ld T = (ld)(mj * mk) * unit;
+                const ld er = -Pr * S + Qr * T;
+                const ld ei = -Pi * S + Qi * T;
+                cplx w = expi_turns(ei / (2.0L * PI_L));
+                row[k] = c_scale(w, (double)expl(er));
+            }
+            for (int64_t s = 0; s < count; ++s) {
+                nsum sr = {0, 0}, si = {0, 0};
+                const cplx* fs = fc + s * N;
+                for (int64_t k = 0; k < N; ++k) {
+                    cplx t = c_mul(row[k], fs[k]);
+                    nsum_add(&sr, t.re);
+                    nsum_add(&si, t.im);
+                }
+                cplx acc = {nsum_get(&sr), nsum_get(&si)};
+                gc[s * N + j] = c_mul(pre, acc);
+            }
+        }
+        free(row);
+    }
+    return fail ? -1 : 0;
+}

@@ -469,3 +469,63 @@ def test_eigenvectors_match_recurrence_in_high_precision(N):
         norm = mpmath.sqrt(mpmath.fsum(v * v for v in p[:N]))
         ref = np.array([float(v / norm) for v in p[:N]])
         assert np.abs(U[:, k] - ref).max() < 1e-12, k
+
+
+# ---- fractional transform for complex z on the real nodes ------------------
+# Sec. 2: the matrix of eq. (fasy) times the samples, eq. (primcuad), the
+# Riemann sum of eq. (eqifft) at y_j = x_j (eq. (cuadtrfor)).
+MEHLER_Z = [0.5, 0.5j, -0.7 + 0.3j, 0.9 * np.exp(0.3j), 0.95 * np.exp(2.5j), 0.3 * np.exp(-1.2j),
+            0.0, np.exp(1.2j), -0.2 - 0.85j]
+
+
+@pytest.mark.parametrize("z", MEHLER_Z)
+def test_mehler_sum_hermite_eigenfunctions(z):
+    """Mehler's formula makes the Hermite functions eigenfunctions of the
+    integral eq. (eqifft): F_z psi_n = sqrt(2 pi) z^n psi_n.  Its Riemann sum
+    on the N = 256 nodes, whose integrand is a resolved Gaussian for these z,
+    reaches that to rounding.  A wrong sign of the cross term (z -> -z)
+    fails every odd n, a dropped (1 + z^2) or a wrong dx or prefactor every n."""
+    N = 256
+    x = O.nodes(N)
+    psi = H.hermite_functions(12, x)
+    g = O.frft_mehler(psi, z)
+    for n in range(13):
+        ref = np.sqrt(2 * np.pi) * complex(z) ** n * psi[n]
+        assert np.linalg.norm(g[n] - ref) < 1e-12 * np.linalg.norm(psi[n]), n
+
+
+@pytest.mark.parametrize("N", [64, 100, 257])
+def test_mehler_sum_parity(N):
+    """The nodes are symmetric (x_{N-1-k} = -x_k) and the exponent of
+    eq. (fasy) is unchanged by (x_j, z) -> (-x_j, -z): F_{-z} is F_z with
+    the output reversed."""
+    x = O.nodes(N)
+    rng = np.random.default_rng(N)
+    f = (rng.standard_normal((3, N)) + 1j * rng.standard_normal((3, N))) * np.exp(-x * x / 4)
+    for z in [0.6 + 0.2j, 0.3 - 0.8j, -0.5]:
+        a = O.frft_mehler(f, -z)
+        b = O.frft_mehler(f, z)[:, ::-1]
+        assert rel_l2(a, b).max() < 1e-15
+
+
+def test_mehler_sum_converges_with_n():
+    """Away from the resolved regime (|z| close to 1 at a small angle) the
+    Riemann sum approaches the eigen-relation as N grows, as eq. (cuadtrfor)
+    states for N -> infinity."""
+    z = 0.99 * np.exp(0.1j)
+    errs = []
+    for N in [128, 256, 512, 1024]:
+        x = O.nodes(N)
+        psi = H.hermite_functions(4, x)
+        g = O.frft_mehler(psi, z)
+        errs.append(max(np.linalg.norm(g[n] - np.sqrt(2 * np.pi) * z ** n * psi[n]) /
+                        np.linalg.norm(psi[n]) for n in range(5)))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-12, errs
+
+
+def test_mehler_sum_rejects_bad_z():
+    x = O.nodes(8)
+    for z in [1.0, -1.0, 1.1, 0.9 + 0.5j]:
+        with pytest.raises(ValueError):
+            O.frft_mehler(x, z)
