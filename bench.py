@@ -44,10 +44,14 @@ COMMON_SOURCES = ["paper_0912_1379_gb300/csrc/xft_common.cuh", "paper_0912_1379_
                   "paper_0912_1379_gb300/csrc/xft_chirp.cuh", "paper_0912_1379_gb300/csrc/xft_async.cuh"]
 KERNEL_SOURCES = ["paper_0912_1379_gb300/csrc/k_fused.cu", "paper_0912_1379_gb300/csrc/k_fused_pair.cu"] + COMMON_SOURCES
 SPLIT_SOURCES = ["paper_0912_1379_gb300/csrc/k_split.cu"] + COMMON_SOURCES
+SPLIT_UMMA_SOURCES = ["paper_0912_1379_gb300/csrc/k_split_umma.cu", "paper_0912_1379_gb300/csrc/xft_umma.cuh",
+                      "paper_0912_1379_gb300/csrc/umma_desc.h"] + COMMON_SOURCES
 # ncu DRAM-traffic summaries, one per kernel: (file, sources whose hash it records)
 TRAFFIC_FILES = {
     "k_xft_fused<12, float>": ("traffic_xft_fused_f32_n4096.json", KERNEL_SOURCES),
     "k_xft_split<12, bf16, 3 products>": ("traffic_xft_split_bf16_n4096.json", SPLIT_SOURCES),
+    "k_xft_split_umma (tcgen05, bf16, 3 products)": ("traffic_xft_split_umma_bf16_n4096.json",
+                                                     SPLIT_UMMA_SOURCES),
     "k_xft_split<12, fp16, 3 products>": ("traffic_xft_split_fp16_n4096.json", SPLIT_SOURCES),
     "k_xft_split<12, fp16, 1 product>": ("traffic_xft_split_fp16x1_n4096.json", SPLIT_SOURCES),
 }
@@ -66,7 +70,11 @@ SPLIT_KERNELS = {"split_bf16": "k_xft_split<12, bf16, 3 products>",
 
 
 def kernel_name(variant, precision):
-    return VARIANT_KERNELS[variant] if variant is not None else SPLIT_KERNELS[precision]
+    if variant is not None:
+        return VARIANT_KERNELS[variant]
+    if precision == "split_bf16" and os.environ.get("LCT_SPLIT_KERNEL", "") != "mma":
+        return "k_xft_split_umma (tcgen05, bf16, 3 products)"     # the library's default
+    return SPLIT_KERNELS[precision]
 
 
 def parse():
@@ -83,20 +91,22 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
     ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8", "9"],
                     help="fused kernel variant (auto: the library's autotuner)")
+    ap.add_argument("--ragged-scale", type=float, default=1.0,
+                    help="ragged workload: scale of every kind's count (1.0: the 20000-instance batch)")
     ap.add_argument("--precision", default="native",
                     choices=["native", "split_bf16", "split_fp16", "fp16"],
                     help="native: FP32 fused kernel (headline); split_*/fp16: the DFT passes "
                          "on the tensor cores")
     ap.add_argument("--workload", default="uniform",
                     choices=["uniform", "ragged", "fields2d", "backward", "config0", "uniform1024",
-                             "hermite", "nonpow2"],
+                             "hermite", "nonpow2", "mehler"],
                     help="uniform: 16384 x N=4096 (headline); ragged: 20000 mixed-N, mixed-kind "
                          "instances in one graph launch; fields2d: separable 2-D LCT forward + "
                          "backward on 8 fields of 2048 x 2048; backward: lct_backward (adjoint "
                          "+ per-signal parameter gradients) on the 16384 x N=4096 batch; config0: "
                          "12 x N=256 complex128 latency; uniform1024: 4096 x N=1024 (L2 flushed); "
                          "hermite: the Hermite-zero FrFT of eq. (tmat), 4096 x N=1024; nonpow2: "
-                         "16384 x N=3000")
+                         "16384 x N=3000; mehler: complex-z FrFT on the real nodes (eq. (primcuad)), 16384 x N=4096")
     return ap.parse_args()
 
 
@@ -346,7 +356,7 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     """The 20000-instance batch.  Under torchrun every rank builds the same
     global batch and transforms its share from lct_partition (cost-balanced,
     largest first): strong scaling, no collective on the data path."""
-    r = W.ragged_plan(seed=W.SEED_RAGGED)
+    r = W.ragged_plan(count_scale=args.ragged_scale, seed=W.SEED_RAGGED)
     M = len(r["kind"])
     Ns = (1 << r["log2n"]).astype(np.int64)
     abcd = r["abcd"].copy()
@@ -427,17 +437,20 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     if rank == 0:
         by_n = {int(n): int((Ns == n).sum()) for n in np.unique(Ns)}
         print(json.dumps({
-            "metric": "LCT points/s, ragged batch (20000 instances, N=2^6..2^16, 4 kinds)",
+            "metric": "LCT points/s, ragged batch (%d instances, N=2^6..2^16, 4 kinds)" % M,
             "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "ragged: 20000 instances (9000 generic, 5000 complex-z FrFT, "
-                                   "4000 Fourier, 2000 b=0), log2 N ~ U{6..16}, seed %d" % W.SEED_RAGGED,
+            "config": {"workload": "ragged: %d instances (%s), log2 N ~ U{6..16}, seed %d"
+                                   % (M, ", ".join("%d %s" % (int((r["kind"] == k).sum()), nm) for k, nm in
+                                                   ((W.KIND_GENERIC, "generic"), (W.KIND_FRFT, "complex-z FrFT"),
+                                                    (W.KIND_FOURIER, "Fourier"), (W.KIND_B0, "b=0"))),
+                                      W.SEED_RAGGED),
                        "points": total, "signals_by_N": by_n,
                        "sharding": "lct_partition over %d ranks (cost N log2 N, largest first); "
                                    "load imbalance %.2e" % (world, load.max() / load.mean() - 1),
-                       "l2": "inputs larger than L2 (1.9 GB per buffer at one GPU), no flush",
+                       "l2": "inputs larger than L2 (%.2f GB per buffer at one GPU), no flush" % (total * 8 / 1e9),
                        "launch": "one persistent kernel over a largest-first work queue" if persistent
                                  else "CUDA graph: one kernel per N group + one b = 0 launch"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -940,6 +953,71 @@ def nonpow2_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
 
 
 # ---------------------------------------------------------------------------
+# complex-z fractional transform on the real nodes (eqs. (fasy), (primcuad))
+# ---------------------------------------------------------------------------
+MEHLER_Z = 0.6 * complex(np.cos(2.2), np.sin(2.2))
+
+
+def mehler_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
+    """16384 complex64 signals of N = 4096 at z = 0.6 e^{2.2i} (Re z < 0: the
+    reversed form); one step = one frft_mehler_execute (the lag kernel's
+    spectrum, one CTA, then the weighted convolution of length M = 8192)."""
+    import oracle as O
+    N, count = 4096, 16384
+    z = MEHLER_Z
+    x = lct.lct_input_grid(N)
+    _, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + 47 + rank, dtype=np.complex64)
+    stream = torch.cuda.current_stream()
+    d_in = torch.from_numpy(f).cuda()
+    d_out = torch.empty_like(d_in)
+
+    def step():
+        lct.frft_mehler_execute(N, z, d_in, d_out, count, lct.LCT_C64, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms, clocks = timed_loop(torch, step, args.steps, stream, local, barrier, max_over_ranks,
+                            args.no_clocks)
+    accuracy = cpu = None
+    if rank == 0 and not args.no_cpu:
+        O.build()
+        # bounded sample: calls of 4 signals (each forms its N^2 kernel entries)
+        # until 10 s of CPU work
+        nsig, refs, t0 = 0, [], time.perf_counter()
+        while nsig < 64 and (nsig == 0 or time.perf_counter() - t0 < 10.0):
+            refs.append(O.frft_mehler(f[nsig:nsig + 4].astype(np.complex128), z))
+            nsig += 4
+        dt = time.perf_counter() - t0
+        ref = np.concatenate(refs)
+        cpu = {"value": nsig * N / dt, "unit": "points/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": "first %d signals of the %d x N=%d workload (dense eq. (fasy) rows, "
+                         "N^2 kernel entries per call), %.1f s" % (nsig, count, N, dt)}
+        accuracy = accuracy_block(rel_l2_rows(d_out[:nsig].cpu().numpy(), ref),
+                                  "FP64 oracle (dense Riemann sum) on the cpu_baseline sample")
+    pts = count * N
+    peak, peak_kind = measured_peak()
+    achieved = pts * BYTES_PER_POINT / (ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "complex-z FrFT points/s on the real nodes at N=4096, 16384 signals complex64; %HBM",
+            "value": world * pts / (ms * 1e-3), "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mehler: 16384 x N=4096 complex64 G1 signals, z = 0.6 e^{2.2i}",
+                       "M": 8192, "l2": "inputs larger than L2 (512 MiB per buffer), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_xft_blue<13, float, Mehler> (16 B/point; two FFTs of M = 8192 "
+                                   "per signal) + k_mehler_spectrum (one CTA)"},
+            "accuracy": accuracy,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -972,7 +1050,7 @@ def main():
 
     arms = {"ragged": ragged_arm, "fields2d": fields2d_arm, "backward": backward_arm,
             "config0": config0_arm, "uniform1024": uniform1024_arm, "hermite": hermite_arm,
-            "nonpow2": nonpow2_arm}
+            "nonpow2": nonpow2_arm, "mehler": mehler_arm}
     if args.workload in arms:
         arms[args.workload](args, rank, world, lct, torch, barrier, max_over_ranks, local)
         if dist is not None:

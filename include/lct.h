@@ -213,6 +213,30 @@ lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                         int64_t batch, lct_dtype dtype, lct_stream_t stream);
 
+/* Fractional transform F_z for complex z on the real nodes, Sec. 2: the
+ * matrix of eq. (fasy) applied to the samples, eq. (primcuad),
+ *     g_j = sqrt(2/(1 - z^2)) dx sum_k e^{E_jk} f(x_k),
+ *     E_jk = -[(1 + z^2)(x_j^2 + x_k^2) - 4 x_j x_k z] / (2 (1 - z^2)),
+ * the Riemann sum of eq. (eqifft) at y_j = x_j (eq. (cuadtrfor)), x_k the
+ * nodes of eq. (asymcer), dx of eq. (deltk).  Unlike frft_execute, whose
+ * output points 4 b(z) x_j / pi are complex for complex z, the output here
+ * is on the input's own real grid.  Computed exactly (up to rounding) in
+ * O(N log N): E_jk = -B x_j^2 - A (x_j - x_k)^2 - B x_k^2 with
+ * A = z/(1 - z^2), B = (1 - z)/(2(1 + z)), so g is a weighted circular
+ * convolution of length M = 2^ceil(log2(2N - 1)); for Re z >= 0 neither
+ * factor grows (Re A, Re B >= 0), and Re z < 0 is run as -z with the output
+ * reversed (the kernel maps to itself under x_j -> -x_j, z -> -z).
+ * in/out: `batch` signals of N samples at x_k (device memory, row-major
+ * [batch][N], complex64 or complex128 computed in that precision, in == out
+ * allowed).  N in [2, 8192] for complex64, [2, 4096] for complex128 (else
+ * LCT_ERR_N); |z| <= 1 and z != +-1 (else LCT_ERR_ARG; on |z| = 1 the same
+ * sum is the real-angle kernel, which aliases for small sin(arg z));
+ * batch in [0, 2^31 - 1].  Two launches on `stream` (the lag kernel's
+ * spectrum, one CTA; the transform) with a workspace of 256 + 8 M (16 M for
+ * complex128) bytes from the stream-ordered allocator; asynchronous. */
+lct_status frft_mehler_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
+                               int64_t batch, lct_dtype dtype, lct_stream_t stream);
+
 /* Hermite-zero discrete fractional Fourier transform of Sec. 2, eq. (tmat):
  *     F_z = sqrt(2 pi) U^T D(z) U,   D(z) = diag(z^0, z^1, ..., z^{N-1}),
  * the exactly unitary (up to sqrt(2 pi), for |z| = 1) discrete transform

@@ -70,6 +70,7 @@ def _load():
             "lct_set_debug": [i32],
             "frft_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "frft_hermite_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
+            "frft_mehler_execute": [i64, f64, f64, vp, vp, i64, i32, vp],
             "frft_hermite_basis": [i64, dp, dp],
             "frft_hermite_status": [vp],
             "lct_transpose": [i32, vp, vp, i64, i64, i64, i64, vp],
@@ -279,6 +280,16 @@ def frft_hermite_execute(N: int, z: complex, inp, out, batch: int, dtype: int = 
     z = complex(z)
     _check(_load().frft_hermite_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
                                         _stream_handle(stream)), "frft_hermite_execute")
+
+
+def frft_mehler_execute(N: int, z: complex, inp, out, batch: int, dtype: int = LCT_C64,
+                        stream=None) -> None:
+    """F_z for complex z on the real nodes y_j = x_j: the matrix of eq. (fasy)
+    times the samples (eq. (primcuad)), as one weighted convolution (see
+    include/lct.h)."""
+    z = complex(z)
+    _check(_load().frft_mehler_execute(N, z.real, z.imag, _ptr(inp), _ptr(out), batch, dtype,
+                                       _stream_handle(stream)), "frft_mehler_execute")
 
 
 def lct_transpose(inp, out, rows: int, cols: int, vec: int = 1, batch: int = 1, dtype: int = LCT_C64,

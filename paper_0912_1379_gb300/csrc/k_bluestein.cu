@@ -52,7 +52,9 @@ __device__ __forceinline__ cpx<R> ld_spec(const cpx<R>* p) {
     return ld_tw<R>(p);
 }
 
-template <int L, class R>
+// MEH: kind LCT_KIND_MEHLER (output weight with its magnitude, optional
+// reversal); a separate instantiation, so the LCT path keeps its registers.
+template <int L, class R, bool MEH>
 __global__ void __launch_bounds__(blue_shape<L>::THREADS, (blue_min_blocks<L, R>()))
 k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
            const lct_desc* __restrict__ desc, int desc_step, int64_t count, int n,
@@ -69,7 +71,8 @@ k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     bool active = sig < count;
     const int64_t gsig = idx ? (active ? idx[sig] : 0) : sig;
     const lct_desc* Dp = desc + (desc_step && active ? gsig : 0);
-    if (active && (Dp->kind != LCT_KIND_BLUE || Dp->n != n || Dp->log2n != L || Dp->offset < 0)) {
+    if (active && (Dp->kind != (MEH ? LCT_KIND_MEHLER : LCT_KIND_BLUE) || Dp->n != n ||
+                   Dp->log2n != L || Dp->offset < 0)) {
         if (i == 0) atomicCAS(status, LCT_DEV_OK, LCT_DEV_BAD_DESC);
         active = false;
     }
@@ -118,7 +121,28 @@ k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
             __syncthreads();          // the first DFT's last exchange is fully read
         }
     }
-    if (active) {
+    if (MEH && active) {
+        const uint64_t out_hi = Dp->out_hi, out_lo = Dp->out_lo, out_c = Dp->out_c;
+        const R sc = (R)Dp->scale;
+        const int fl = Dp->flags;
+        const bool odecay = (fl & LCT_FLAG_OUT_DECAY) != 0;   // kind LCT_KIND_MEHLER
+        const int rev = (fl & LCT_FLAG_REVERSE) ? n - 1 : 0;
+        const double dec = Dp->decay;
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) {
+            const int j = i + e * S::T;
+            const cpx<R> y = {v[e].x, -v[e].y};         // the conj of the inverse's form
+            if (j < n) {
+                cpx<R> w = chirp_any<R>(out_hi, out_lo, out_c, j, n);
+                if (odecay) {
+                    const uint32_t m2 = m_squared(j, n);
+                    if constexpr (sizeof(R) == 4) w = cscale(w, expf(-(float)dec * (float)m2));
+                    else w = cscale(w, exp(-dec * (double)m2));
+                }
+                out[base + (rev ? rev - j : j)] = cscale(cmul(y, w), sc);
+            }
+        }
+    } else if (active) {
         const uint64_t out_hi = Dp->out_hi, out_lo = Dp->out_lo, out_c = Dp->out_c;
         const R sc = (R)Dp->scale;
 #pragma unroll
@@ -130,14 +154,14 @@ k_xft_blue(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
     }
 }
 
-template <int L, class R>
+template <int L, class R, bool MEH>
 cudaError_t launch_blue_l(int n, const void* in, void* out, const lct_desc* desc, int desc_step,
                           int64_t count, const void* tw, const void* spec, const int32_t* idx,
                           int32_t* status, cudaStream_t stream) {
     using S = shape<L>;
     using F = blue_shape<L>;
     const size_t smem = S::P > 1 ? (size_t)F::SPC * S::NP * sizeof(cpx<R>) : 0;
-    auto kern = k_xft_blue<L, R>;
+    auto kern = k_xft_blue<L, R, MEH>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -151,20 +175,100 @@ cudaError_t launch_blue_l(int n, const void* in, void* out, const lct_desc* desc
     return cudaGetLastError();
 }
 
-template <class R>
+template <class R, bool MEH>
 cudaError_t blue_dispatch(int n, const void* in, void* out, const lct_desc* desc, int desc_step,
                           int64_t count, const void* tw, const void* spec, const int32_t* idx,
                           int32_t* status, cudaStream_t stream) {
     switch (lct_blue_log2m(n)) {
 #define LCT_CASE(L) \
-    case L: return launch_blue_l<L, R>(n, in, out, desc, desc_step, count, tw, spec, idx, status, stream);
-        LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8)
+    case L: return launch_blue_l<L, R, MEH>(n, in, out, desc, desc_step, count, tw, spec, idx, status, stream);
+        LCT_CASE(2) LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8)
         LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12) LCT_CASE(13)
 #undef LCT_CASE
         case 14:
             if constexpr (sizeof(R) == 4)
-                return launch_blue_l<14, R>(n, in, out, desc, desc_step, count, tw, spec, idx, status,
-                                            stream);
+                return launch_blue_l<14, R, MEH>(n, in, out, desc, desc_step, count, tw, spec, idx,
+                                                 status, stream);
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Kernel spectrum of the complex-z fractional transform on the nodes (kind
+// LCT_KIND_MEHLER, lct_internal.h): one CTA forms h_l = e^{-a_h l^2}
+// e^{2 pi i phi_h l^2} at the circular positions of the lags |l| < n (the
+// phase from the exact turn fraction, the magnitude in FP64), takes DFT_M
+// with the same engine, and stores c/M times it.  Thread 0 also stores the
+// signal descriptor and clears the status word, so the host needs no copy.
+template <int L, class R>
+__global__ void __launch_bounds__(shape<L>::T)
+k_mehler_spectrum(int n, double a_h, uint64_t phi_hi, uint64_t phi_lo, double c_re, double c_im,
+                  const lct_desc D, lct_desc* __restrict__ d_desc, cpx<R>* __restrict__ spec,
+                  int32_t* __restrict__ status, const cpx<R>* __restrict__ tw) {
+    using S = shape<L>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<R>* buf = reinterpret_cast<cpx<R>*>(smem_raw);
+    const int i = threadIdx.x;
+    if (i == 0) {
+        *d_desc = D;
+        *status = LCT_DEV_OK;
+    }
+    cpx<R> v[S::E];
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const int t = i + e * S::T;
+        const int l = t < n ? t : (t > S::N - n ? t - S::N : 0x40000000);
+        cpx<R> h = {R(0), R(0)};
+        if (l != 0x40000000) {
+            const uint32_t l2 = (uint32_t)(l * l);
+            const cpx<double> w = expi_turn64(phase64(phi_hi, phi_lo, l2));
+            const double mag = exp(-a_h * (double)l2);
+            h = {(R)(w.x * mag), (R)(w.y * mag)};
+        }
+        v[e] = h;
+    }
+    dft_signal<L, -1>(v, buf, i, tw);
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const double x = (double)v[e].x, y = (double)v[e].y;
+        spec[i + e * S::T] = {(R)(x * c_re - y * c_im), (R)(x * c_im + y * c_re)};
+    }
+}
+
+template <int L, class R>
+cudaError_t launch_mehler_spec_l(int n, double a_h, uint64_t phi_hi, uint64_t phi_lo, double c_re,
+                                 double c_im, const lct_desc& D, lct_desc* d_desc, void* spec,
+                                 int32_t* status, const void* tw, cudaStream_t stream) {
+    using S = shape<L>;
+    const size_t smem = S::P > 1 ? (size_t)S::NP * sizeof(cpx<R>) : 0;
+    auto kern = k_mehler_spectrum<L, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const double inv_m = 1.0 / (double)S::N;
+    kern<<<1, S::T, smem, stream>>>(n, a_h, phi_hi, phi_lo, c_re * inv_m, c_im * inv_m, D, d_desc,
+                                    (cpx<R>*)spec, status, (const cpx<R>*)tw);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t mehler_spec_dispatch(int n, double a_h, uint64_t phi_hi, uint64_t phi_lo, double c_re,
+                                 double c_im, const lct_desc& D, lct_desc* d_desc, void* spec,
+                                 int32_t* status, const void* tw, cudaStream_t stream) {
+    switch (lct_blue_log2m(n)) {
+#define LCT_CASE(L)                                                                                \
+    case L:                                                                                        \
+        return launch_mehler_spec_l<L, R>(n, a_h, phi_hi, phi_lo, c_re, c_im, D, d_desc, spec, status, \
+                                          tw, stream);
+        LCT_CASE(2) LCT_CASE(3) LCT_CASE(4) LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8)
+        LCT_CASE(9) LCT_CASE(10) LCT_CASE(11) LCT_CASE(12) LCT_CASE(13)
+#undef LCT_CASE
+        case 14:
+            if constexpr (sizeof(R) == 4)
+                return launch_mehler_spec_l<14, R>(n, a_h, phi_hi, phi_lo, c_re, c_im, D, d_desc, spec,
+                                                   status, tw, stream);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
@@ -197,10 +301,38 @@ cudaError_t lct_launch_blue(int dtype, int64_t n, const void* in, void* out, con
                             const int32_t* idx, int32_t* status, cudaStream_t stream) {
     if (!lct_blue_supported(dtype, n) || !spec) return cudaErrorInvalidValue;
     if (dtype == 0)
-        return blue_dispatch<float>((int)n, in, out, desc, desc_step, count, tw, spec, idx, status,
-                                    stream);
-    return blue_dispatch<double>((int)n, in, out, desc, desc_step, count, tw, spec, idx, status,
-                                 stream);
+        return blue_dispatch<float, false>((int)n, in, out, desc, desc_step, count, tw, spec, idx,
+                                           status, stream);
+    return blue_dispatch<double, false>((int)n, in, out, desc, desc_step, count, tw, spec, idx,
+                                        status, stream);
+}
+
+static bool mehler_size_ok(int dtype, int64_t n) {
+    return n >= 2 && n <= (dtype == 0 ? kBlueMaxN64 : kBlueMaxN128);
+}
+
+cudaError_t lct_launch_mehler(int dtype, int64_t n, const void* in, void* out, const lct_desc* desc,
+                              int64_t count, const void* tw, const void* spec, int32_t* status,
+                              cudaStream_t stream) {
+    if (!mehler_size_ok(dtype, n) || !spec) return cudaErrorInvalidValue;
+    if (count <= 0) return cudaSuccess;
+    if (dtype == 0)
+        return blue_dispatch<float, true>((int)n, in, out, desc, 0, count, tw, spec, nullptr, status,
+                                          stream);
+    return blue_dispatch<double, true>((int)n, in, out, desc, 0, count, tw, spec, nullptr, status,
+                                       stream);
+}
+
+cudaError_t lct_launch_mehler_spectrum(int dtype, int64_t n, double a_h, uint64_t phi_hi,
+                                       uint64_t phi_lo, double c_re, double c_im,
+                                       const lct_desc& D, lct_desc* d_desc, void* spec,
+                                       int32_t* status, const void* tw, cudaStream_t stream) {
+    if (!mehler_size_ok(dtype, n) || !spec || !d_desc || !status) return cudaErrorInvalidValue;
+    if (dtype == 0)
+        return mehler_spec_dispatch<float>((int)n, a_h, phi_hi, phi_lo, c_re, c_im, D, d_desc, spec,
+                                           status, tw, stream);
+    return mehler_spec_dispatch<double>((int)n, a_h, phi_hi, phi_lo, c_re, c_im, D, d_desc, spec,
+                                        status, tw, stream);
 }
 
 cudaError_t lct_launch_diag_any(int dtype, int64_t n, const void* in, void* out,

@@ -719,4 +719,43 @@ lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, voi
     return st;
 }
 
+// Complex-z fractional transform on the nodes (Sec. 2, eqs. (fasy),
+// (primcuad)) as one convolution of length M = 2^ceil(log2(2N - 1)): a
+// one-CTA launch forms the lag kernel's spectrum and the descriptor in a
+// stream-ordered workspace, then the chirp-convolution kernel transforms the
+// batch (lct_internal.h derives the form).
+lct_status frft_mehler_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
+                               int64_t batch, lct_dtype dtype, lct_stream_t stream_) {
+    trace_range trace("frft_mehler_execute");
+    if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
+    if (N < 2 || N > (dtype == LCT_C64 ? kBlueMaxN64 : kBlueMaxN128)) return LCT_ERR_N;
+    lct_desc D;
+    mehler_consts K;
+    lct_status st = mehler_setup(N, z_re, z_im, &D, &K);
+    if (st != LCT_OK) return st;
+    if (batch < 0 || batch > (int64_t)0x7fffffff) return LCT_ERR_ARG;
+    if (batch == 0) return LCT_OK;
+    st = check_ptr(in, dtype);
+    if (st == LCT_OK) st = check_ptr(out, dtype);
+    if (st != LCT_OK) return st;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int lm = D.log2n;
+    const void* tw = lct_twiddle_table(dtype, lm);
+    if (lm >= 5 && !tw) return LCT_ERR_OOM;
+    // workspace: descriptor (80 B), status word, spectrum (M samples) at 256 B
+    const size_t spec_bytes = ((size_t)1 << lm) * sample_bytes(dtype);
+    void* ws = nullptr;
+    if (cudaMallocAsync(&ws, 256 + spec_bytes, stream) != cudaSuccess) return LCT_ERR_OOM;
+    lct_desc* d_desc = (lct_desc*)ws;
+    int32_t* d_status = (int32_t*)((char*)ws + 128);
+    void* spec = (char*)ws + 256;
+    cudaError_t e = lct_launch_mehler_spectrum(dtype, N, K.a_h, K.phi_hi, K.phi_lo, K.c_re, K.c_im,
+                                               D, d_desc, spec, d_status, tw, stream);
+    if (e == cudaSuccess)
+        e = lct_launch_mehler(dtype, N, in, out, d_desc, batch, tw, spec, d_status, stream);
+    const cudaError_t ef = cudaFreeAsync(ws, stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(ef);
+}
+
 }  // extern "C"

@@ -29,12 +29,26 @@
 // convolution runs as a circular one of length M = 2^log2n >= 2N - 1
 // (Bluestein's algorithm): kind LCT_KIND_BLUE, n = N.  b == 0 signals of such
 // N are kind LCT_KIND_DIAGN (the diagonal above, log2n unused).
+//
+// Fractional transform for complex z on the real nodes (Sec. 2, eqs. (fasy),
+// (primcuad)): the kernel e^{-[(1+z^2)(x_j^2+x_k^2) - 4 x_j x_k z]/(2(1-z^2))}
+// is exactly e^{-B x_j^2} e^{-A (x_j - x_k)^2} e^{-B x_k^2} with
+// A = z/(1 - z^2), B = (1 - z)/(2 (1 + z)), so with x = pi m/(2 sqrt(2N)) the
+// same convolution form holds with real weights:
+//   G_j = e^{2 pi i phi m_j^2} e^{-decay m_j^2} sum_k h_{j-k} e^{2 pi i phi m_k^2} e^{-decay m_k^2} f_k,
+//   phi = -Im(B) pi/(16N) turns (in_hi/lo = out_hi/lo), decay = Re(B) pi^2/(8N),
+//   h_n = e^{-A pi^2 n^2/(2N)} times sqrt(2/(1 - z^2)) dx,
+// kind LCT_KIND_MEHLER, flags DECAY and OUT_DECAY.  For Re z >= 0, Re A >= 0
+// and Re B >= 0, so no factor grows; Re z < 0 runs -z and reverses the output
+// (the kernel is odd in z through x_j -> -x_j: flag REVERSE).
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
 
-enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1, LCT_KIND_BLUE = 2, LCT_KIND_DIAGN = 3 };
-enum { LCT_FLAG_DECAY = 1 };
+enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1, LCT_KIND_BLUE = 2, LCT_KIND_DIAGN = 3, LCT_KIND_MEHLER = 4 };
+// DECAY: the input weight carries e^{-decay m^2}; OUT_DECAY: the output
+// weight too (kind LCT_KIND_MEHLER); REVERSE: sample j is stored at N-1-j.
+enum { LCT_FLAG_DECAY = 1, LCT_FLAG_OUT_DECAY = 2, LCT_FLAG_REVERSE = 4 };
 
 struct __align__(16) lct_desc {
     uint64_t in_hi, in_lo;    // phi_in  (128-bit turn fraction)
@@ -264,6 +278,20 @@ const void* lct_blue_spectrum(int dtype, int64_t n);
 cudaError_t lct_launch_blue(int dtype, int64_t n, const void* in, void* out, const lct_desc* desc,
                             int desc_step, int64_t count, const void* tw, const void* spec,
                             const int32_t* idx, int32_t* status, cudaStream_t stream);
+// The same kernel for kind LCT_KIND_MEHLER descriptors (any N = 2 ..
+// kBlueMaxN64 / kBlueMaxN128, powers of two included) with the spectrum of
+// lct_launch_mehler_spectrum.
+cudaError_t lct_launch_mehler(int dtype, int64_t n, const void* in, void* out, const lct_desc* desc,
+                              int64_t count, const void* tw, const void* spec, int32_t* status,
+                              cudaStream_t stream);
+// One CTA: spec[t] = c/M DFT_M(h)[t] for h_l = e^{-a_h l^2} e^{2 pi i phi_h l^2}
+// placed circularly (|l| < n, zero elsewhere), M = 2^lct_blue_log2m(n),
+// phi_h a 128-bit turn fraction, c = (c_re, c_im); also stores `D` at
+// d_desc and zeroes *status (all in device memory).
+cudaError_t lct_launch_mehler_spectrum(int dtype, int64_t n, double a_h, uint64_t phi_hi,
+                                       uint64_t phi_lo, double c_re, double c_im,
+                                       const lct_desc& D, lct_desc* d_desc, void* spec,
+                                       int32_t* status, const void* tw, cudaStream_t stream);
 // b == 0 signals of one N that is not a power of two (kind LCT_KIND_DIAGN).
 cudaError_t lct_launch_diag_any(int dtype, int64_t n, const void* in, void* out,
                                 const lct_desc* desc, int desc_step, int64_t count,

@@ -209,6 +209,57 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
     return LCT_OK;
 }
 
+// Complex-z fractional transform on the nodes (Sec. 2, eqs. (fasy),
+// (primcuad)); the convolution form is derived in lct_internal.h.  With
+// z = x + i y (after the parity step x >= 0):
+//   B = (1 - z)/(2(1 + z)):  Re B = (1 - |z|^2)/(2|1 + z|^2),  Im B = -y/|1 + z|^2
+//   A = z/(1 - z^2):         Re A = x (1 - |z|^2)/|1 - z^2|^2,
+//                            Im A = y (1 + |z|^2)/|1 - z^2|^2
+// The phase coefficients are formed in double-double from the FP64 z and
+// reduced to 128-bit turn fractions; the magnitudes in FP64.
+lct_status mehler_setup(int64_t N, double z_re, double z_im, lct_desc* D, mehler_consts* K) {
+    if (!std::isfinite(z_re) || !std::isfinite(z_im)) return LCT_ERR_ARG;
+    if (std::hypot(z_re, z_im) > 1.0 + 1e-15) return LCT_ERR_ARG;
+    if (z_im == 0.0 && std::fabs(z_re) == 1.0) return LCT_ERR_ARG;       // 1 - z^2 = 0
+    const bool rev = z_re < 0.0;
+    const double x = rev ? -z_re : z_re, y = rev ? -z_im : z_im;
+    const dd one = {1.0, 0.0}, X = {x, 0.0}, Y = {y, 0.0}, DN = {(double)N, 0.0};
+    const dd x2 = two_prod(x, x), y2 = two_prod(y, y);
+    const dd r2 = dd_add(x2, y2);                                // |z|^2
+    dd omr2 = dd_sub(one, r2);                                   // 1 - |z|^2
+    if (omr2.hi < 0.0) omr2 = {0.0, 0.0};                        // |z| = 1 up to rounding
+    const dd opx = two_sum(1.0, x);
+    const dd q = dd_add(dd_mul(opx, opx), y2);                   // |1 + z|^2
+    const dd u = dd_add(dd_sub(one, x2), y2);                    // Re(1 - z^2)
+    const dd v = dd_ldexp(two_prod(x, y), 1);                    // -Im(1 - z^2)
+    const dd den = dd_add(dd_mul(u, u), dd_mul(v, v));           // |1 - z^2|^2
+    const double re_b = dd_div(omr2, dd_ldexp(q, 1)).hi;
+    const dd im_b = dd_neg(dd_div(Y, q));
+    const double re_a = dd_div(dd_mul(X, omr2), den).hi;
+    const dd im_a = dd_div(dd_mul(Y, dd_add(one, r2)), den);
+    std::memset(D, 0, sizeof(*D));
+    D->kind = LCT_KIND_MEHLER;
+    D->n = (int32_t)N;
+    D->log2n = lct_blue_log2m(N);
+    D->scale = 1.0;
+    // weight e^{-B x^2}, x^2 = pi^2 m^2/(8N): phase -Im(B) pi/(16N) turns per m^2
+    uint64_t hi, lo;
+    dd_to_turns128(dd_div(dd_mul(dd_neg(im_b), DD_PI), dd_ldexp(DN, 4)), &hi, &lo);
+    D->in_hi = D->out_hi = hi;
+    D->in_lo = D->out_lo = lo;
+    D->decay = re_b * M_PI * M_PI / (8.0 * (double)N);
+    if (D->decay != 0.0) D->flags |= LCT_FLAG_DECAY | LCT_FLAG_OUT_DECAY;
+    if (rev) D->flags |= LCT_FLAG_REVERSE;
+    // lag kernel e^{-A (x_j - x_k)^2}, (x_j - x_k)^2 = pi^2 l^2/(2N)
+    K->a_h = re_a * M_PI * M_PI / (2.0 * (double)N);
+    dd_to_turns128(dd_div(dd_mul(dd_neg(im_a), DD_PI), dd_ldexp(DN, 2)), &K->phi_hi, &K->phi_lo);
+    // sqrt(2/(1 - z^2)) dx, principal root (1 - z^2 is even in z)
+    const cplx c = std::sqrt(2.0 / cplx(u.hi, -v.hi)) * (M_PI / std::sqrt(2.0 * (double)N));
+    K->c_re = c.real();
+    K->c_im = c.imag();
+    return LCT_OK;
+}
+
 }  // namespace lcth
 
 using namespace lcth;

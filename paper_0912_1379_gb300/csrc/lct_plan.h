@@ -111,6 +111,14 @@ uint64_t double_to_turns64(double v);
 // Validates p = {a, b, c, d} (re, im pairs; ad - bc = 1) and fills the
 // descriptor of one N-point signal at element `offset`.
 lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D);
+// Complex-z fractional transform on the nodes (kind LCT_KIND_MEHLER): the
+// descriptor and the lag-kernel constants h_l = c e^{-a_h l^2} e^{2 pi i phi_h l^2}.
+struct mehler_consts {
+    double a_h, c_re, c_im;
+    uint64_t phi_hi, phi_lo;
+};
+// |z| <= 1 (+1e-15), z != +-1, finite; else LCT_ERR_ARG.  N is not checked.
+lct_status mehler_setup(int64_t N, double z_re, double z_im, lct_desc* D, mehler_consts* K);
 
 // ---- lct_plan.cpp ---------------------------------------------------------
 int tune_lookup(int dtype, int log2n);               // -1: no cached choice

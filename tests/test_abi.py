@@ -323,3 +323,28 @@ def test_partition_costs_non_power_of_two():
     """A non-power-of-two N costs two DFTs of M >= 2N - 1 (here M = 2048)."""
     owner, load = lct.lct_partition([1000, 1024], 2)
     assert sorted(load.tolist()) == [1024 * 10, 2 * 2048 * 11]
+
+
+@pytest.mark.parametrize("N,z,dtype,status", [
+    (1, 0.5, lct.LCT_C64, 2), (8193, 0.5, lct.LCT_C64, 2), (4097, 0.5, lct.LCT_C128, 2),
+    (64, 1.0, lct.LCT_C64, 1), (64, -1.0, lct.LCT_C128, 1), (64, 1.2j, lct.LCT_C64, 1),
+    (64, 0.8 + 0.7j, lct.LCT_C64, 1), (64, complex(float("nan"), 0.0), lct.LCT_C64, 1),
+    (64, 0.5, 9, 4)])
+def test_frft_mehler_validation_without_gpu(N, z, dtype, status):
+    """Size, z and dtype are checked before any device call."""
+    with pytest.raises(lct.LctError) as e:
+        lct.frft_mehler_execute(N, z, 64, 64, 1, dtype=dtype, stream=0)
+    assert e.value.status == status
+
+
+def test_frft_mehler_batch_and_pointers_without_gpu():
+    # batch 0 is a no-op after validation; a negative batch or a null
+    # pointer is LCT_ERR_ARG, all without a device call
+    for N, dtype in [(2, lct.LCT_C64), (8192, lct.LCT_C64), (4096, lct.LCT_C128), (3000, lct.LCT_C64)]:
+        lct.frft_mehler_execute(N, 0.3 + 0.4j, 0, 0, 0, dtype=dtype, stream=0)
+    for z in [np.exp(0.7j), -0.6j, 0.0]:
+        lct.frft_mehler_execute(256, z, 0, 0, 0, stream=0)
+    for batch, ptr in [(-1, 64), (1, 0)]:
+        with pytest.raises(lct.LctError) as e:
+            lct.frft_mehler_execute(64, 0.5, ptr, ptr, batch, stream=0)
+        assert e.value.status == 1
