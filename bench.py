@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
     ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8", "9"],
                     help="fused kernel variant (auto: the library's autotuner)")
+    ap.add_argument("--nonpow2-n", type=int, default=3000,
+                    help="nonpow2 workload: N (7-smooth: mixed radix; else chirp convolution)")
     ap.add_argument("--ragged-scale", type=float, default=1.0,
                     help="ragged workload: scale of every kind's count (1.0: the 20000-instance batch)")
     ap.add_argument("--precision", default="native",
@@ -902,10 +904,21 @@ def hermite_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
 # N that is not a power of two (chirp convolution of length M >= 2N - 1)
 # ---------------------------------------------------------------------------
 def nonpow2_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
-    """16384 complex64 signals of N = 3000 (M = 8192), G1 per-signal
-    parameters; one step = one lct_execute (the fused chirp-convolution
-    kernel: pre-chirp, FFT_M, spectrum, inverse FFT_M, post-chirp)."""
-    N, count = 3000, 16384
+    """16384 complex64 signals of N = 3000 (default; --nonpow2-n), G1
+    per-signal parameters; one step = one lct_execute.  7-smooth N (3000 =
+    2^3 3 5^3) runs the mixed-radix kernel (chirp, DFT_N in passes of radix
+    8, 5, 5, 5, 3, chirp); other N the chirp convolution (pre-chirp, FFT_M,
+    spectrum, inverse FFT_M, post-chirp, M >= 2N - 1)."""
+    N, count = args.nonpow2_n, 16384
+    smooth = N
+    for q in (2, 3, 5, 7):
+        while smooth % q == 0:
+            smooth //= q
+    M = 1
+    while M < 2 * N - 1:
+        M *= 2
+    kernel = ("k_xft_mixed<float> (16 B/point; one mixed-radix DFT of N per signal)" if smooth == 1 else
+              "k_xft_blue<%d, float> (16 B/point; two FFTs of M = %d per signal)" % (M.bit_length() - 1, M))
     x = lct.lct_input_grid(N)
     params, f = W.uniform_batch(x, count, seed=W.SEED_UNIFORM_4096 + 31 + rank, dtype=np.complex64)
     plan = lct.Plan.batch([N] * count, params, np.arange(count, dtype=np.int64) * N, dtype=lct.LCT_C64)
@@ -936,15 +949,16 @@ def nonpow2_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
     achieved = pts * BYTES_PER_POINT / (ms * 1e-3) / 1e9
     if rank == 0:
         print(json.dumps({
-            "metric": "LCT points/s at N=3000 (not a power of two), 16384 signals complex64; %HBM",
+            "metric": "LCT points/s at N=%d (not a power of two), 16384 signals complex64; %%HBM" % N,
             "value": world * pts / (ms * 1e-3), "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "nonpow2: 16384 x N=3000 complex64, G1 per-signal (a,b,c,d)",
-                       "M": 8192, "l2": "inputs larger than L2 (393 MB per buffer), no flush"},
+            "config": {"workload": "nonpow2: 16384 x N=%d complex64, G1 per-signal (a,b,c,d)" % N,
+                       "path": "mixed radix" if smooth == 1 else "chirp convolution, M = %d" % M,
+                       "l2": "inputs larger than L2 (%d MB per buffer), no flush" % (count * N * 8 // 10**6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_xft_blue<13, float> (16 B/point; two FFTs of M = 8192 per signal)"},
+                         "kernel": kernel},
             "accuracy": accuracy,
             "cpu_baseline": cpu,
             "clocks": clocks,

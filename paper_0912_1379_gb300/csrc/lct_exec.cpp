@@ -215,6 +215,14 @@ lct_status run_blue(lct_plan p, int kind, int64_t n, const void* in, void* out, 
     if (kind == LCT_KIND_DIAGN)
         return from_cuda(lct_launch_diag_any(p->dtype, n, in, out, p->d_desc, desc_step, count, idx,
                                              p->d_status, stream));
+    if (kind == LCT_KIND_MIXED) {
+        lct_mixed_plan pl;
+        if (!lct_mixed_make_plan(n, p->dtype, &pl)) return LCT_ERR_N;
+        const void* tw = lct_mixed_twiddles(p->dtype, n);
+        if (!tw) return LCT_ERR_OOM;
+        return from_cuda(lct_launch_mixed(p->dtype, pl, in, out, p->d_desc, desc_step, count, tw, idx,
+                                          p->d_status, stream));
+    }
     const int lm = lct_blue_log2m(n);
     const void* tw = lct_twiddle_table(p->dtype, lm);
     const void* spec = lct_blue_spectrum(p->dtype, n);
@@ -274,6 +282,10 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
     }
     for (const auto& g : p->groups) {
         if (g.kind == LCT_KIND_DIAG || g.kind == LCT_KIND_DIAGN) continue;
+        if (g.kind == LCT_KIND_MIXED) {
+            if (!lct_mixed_twiddles(p->dtype, g.n)) return LCT_ERR_OOM;
+            continue;
+        }
         if (g.kind == LCT_KIND_BLUE) {
             if ((g.log2n >= 5 && !lct_twiddle_table(p->dtype, g.log2n)) ||
                 !lct_blue_spectrum(p->dtype, g.n))

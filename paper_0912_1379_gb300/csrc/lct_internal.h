@@ -30,6 +30,14 @@
 // (Bluestein's algorithm): kind LCT_KIND_BLUE, n = N.  b == 0 signals of such
 // N are kind LCT_KIND_DIAGN (the diagonal above, log2n unused).
 //
+// N = 2^a 3^b 5^c 7^d that is not a power of two: the direct form above with
+// a mixed-radix DFT (k_mixed.cu), kind LCT_KIND_MIXED, log2n = ceil(log2 N)
+// (group order only): phi_in,
+// phi_out, decay and scale as for LCT_KIND_XFT (N in place of 2^log2n), the
+// centring phases (N-1) k/(2N) formed in the kernel, and
+// scale e^{2 pi i c_out} = dx e^{-i pi (N-1)^2/(2N)} / sqrt(2 pi i b).  Other N
+// keep the chirp-convolution form (LCT_KIND_BLUE).
+//
 // Fractional transform for complex z on the real nodes (Sec. 2, eqs. (fasy),
 // (primcuad)): the kernel e^{-[(1+z^2)(x_j^2+x_k^2) - 4 x_j x_k z]/(2(1-z^2))}
 // is exactly e^{-B x_j^2} e^{-A (x_j - x_k)^2} e^{-B x_k^2} with
@@ -45,7 +53,8 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
-enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1, LCT_KIND_BLUE = 2, LCT_KIND_DIAGN = 3, LCT_KIND_MEHLER = 4 };
+enum { LCT_KIND_XFT = 0, LCT_KIND_DIAG = 1, LCT_KIND_BLUE = 2, LCT_KIND_DIAGN = 3, LCT_KIND_MEHLER = 4,
+       LCT_KIND_MIXED = 5 };
 // DECAY: the input weight carries e^{-decay m^2}; OUT_DECAY: the output
 // weight too (kind LCT_KIND_MEHLER); REVERSE: sample j is stored at N-1-j.
 enum { LCT_FLAG_DECAY = 1, LCT_FLAG_OUT_DECAY = 2, LCT_FLAG_REVERSE = 4 };
@@ -292,6 +301,38 @@ cudaError_t lct_launch_mehler_spectrum(int dtype, int64_t n, double a_h, uint64_
                                        uint64_t phi_lo, double c_re, double c_im,
                                        const lct_desc& D, lct_desc* d_desc, void* spec,
                                        int32_t* status, const void* tw, cudaStream_t stream);
+// Mixed-radix plan of one N (kind LCT_KIND_MIXED): the passes' radices
+// (16, 8, 4, 2, 7, 5, 3), Ns_p (product of the earlier radices), the exact
+// divisor magic floor(2^32 / Ns_p) + 1 (b / Ns_p = umulhi(b, magic) for
+// b < 2^32 / Ns_p), each pass's offset into the twiddle table, the 128-bit
+// turn fraction 1/(2N), and the threads per signal (>= N / (R K_R) for every
+// pass, K_R = 16 / R butterflies a thread, a multiple of 32).
+constexpr int kMixedMaxPasses = 16;
+struct __align__(16) lct_mixed_plan {
+    int n, npass, threads, pad;
+    int radix[kMixedMaxPasses];
+    int ns[kMixedMaxPasses];
+    uint32_t magic[kMixedMaxPasses];
+    int twoff[kMixedMaxPasses];
+    uint64_t inv_hi, inv_lo;
+};
+static_assert(sizeof(lct_mixed_plan) <= 512, "plan header");
+// Host: is N a non-power-of-two 7-smooth size in [3, 8192]?
+bool lct_mixed_ok(int64_t n);
+// Host: the plan of such an N (false otherwise).
+bool lct_mixed_make_plan(int64_t n, int dtype, lct_mixed_plan* pl);
+// Host: device buffer of that plan (cached per device, dtype and N): the
+// lct_mixed_plan itself, then at byte kMixedPlanBytes the twiddle table in
+// the dtype's precision: for pass p >= 1, entry [twoff_p + (r - 1) Ns_p + j]
+// = e^{-2 pi i j r / (Ns_p R_p)}.
+constexpr size_t kMixedPlanBytes = 512;
+const void* lct_mixed_twiddles(int dtype, int64_t n);
+// Threads per CTA of the mixed-radix kernel for a plan (several signals per
+// CTA below 256 threads per signal).
+int lct_mixed_threads_per_cta(const lct_mixed_plan& pl);
+cudaError_t lct_launch_mixed(int dtype, const lct_mixed_plan& pl, const void* in, void* out,
+                             const lct_desc* desc, int desc_step, int64_t count, const void* tw,
+                             const int32_t* idx, int32_t* status, cudaStream_t stream);
 // b == 0 signals of one N that is not a power of two (kind LCT_KIND_DIAGN).
 cudaError_t lct_launch_diag_any(int dtype, int64_t n, const void* in, void* out,
                                 const lct_desc* desc, int desc_step, int64_t count,

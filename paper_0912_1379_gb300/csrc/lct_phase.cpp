@@ -172,6 +172,25 @@ lct_status make_desc(int64_t N, const double* p, int64_t offset, lct_desc* D) {
     double dx = M_PI / std::sqrt(2.0 * (double)N);
     cplx pre = dx / std::sqrt(cplx(0.0, 2.0 * M_PI) * b);
     D->scale = std::abs(pre);
+    if (!pow2 && lct_mixed_ok(N)) {
+        // direct form with a mixed-radix DFT: the XFT phases with N in place
+        // of 2^log2n; the centring phases are formed in the kernel
+        D->kind = LCT_KIND_MIXED;
+        D->log2n = lct_blue_log2m(N) - 1;          // ceil(log2 N): orders the plan's groups
+        dd tin = dd_div(dd_ldexp(dd_mul(dd_re_div(a, b), DD_PI), -5), DN);   // Re(a/b) pi/(32N)
+        dd_to_turns128(tin, &hi, &lo);
+        D->in_hi = hi;
+        D->in_lo = lo;
+        dd tout = dd_div(dd_div(dd_re_mul(b, d), dd_ldexp(DD_PI, 1)), DN);  // Re(bd)/(2 pi N)
+        dd_to_turns128(tout, &hi, &lo);
+        D->out_hi = hi;
+        D->out_lo = lo;
+        // constant -(N-1)^2/(4N) turns: -r/(4N), r = (N-1)^2 mod 4N, in Q0.64
+        const uint64_t r = (uint64_t)(((N - 1) * (N - 1)) % (4 * N));
+        const uint64_t centre = (uint64_t)0 - (uint64_t)((((unsigned __int128)r) << 64) / (uint64_t)(4 * N));
+        D->out_c = centre + double_to_turns64(std::arg(pre) / (2.0 * M_PI));
+        return LCT_OK;
+    }
     if (!pow2) {
         // chirp-convolution form: phi_in - 1/(8N), phi_out - 1/(8N), constant
         // arg(dx / sqrt(2 pi i b)) only
@@ -431,6 +450,89 @@ const void* lct_blue_spectrum(int dtype, int64_t n) {
     const auto key = std::make_tuple(dev, 100 + dtype, (int)n);
     if (dtype == LCT_C64) return cached_table(key, [&] { return build_blue_spectrum<float>(n); });
     return cached_table(key, [&] { return build_blue_spectrum<double>(n); });
+}
+
+// ---------------------------------------------------------------------------
+// mixed-radix plans and twiddles for 7-smooth N that is not a power of two
+// ---------------------------------------------------------------------------
+bool lct_mixed_ok(int64_t n) {
+    if (n < 3 || n > 8192 || ilog2_exact(n) >= 0) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+bool lct_mixed_make_plan(int64_t n, int dtype, lct_mixed_plan* pl) {
+    if (!lct_mixed_ok(n)) return false;
+    std::memset(pl, 0, sizeof(*pl));
+    pl->n = (int)n;
+    // radices: the power of two as 16s, then one 8, 4 or 2; then 7s, 5s, 3s
+    int64_t m = n;
+    int twos = 0;
+    while (m % 2 == 0) { m /= 2; ++twos; }
+    int np = 0;
+    while (twos >= 4) { pl->radix[np++] = 16; twos -= 4; }
+    if (twos > 0) pl->radix[np++] = 1 << twos;
+    for (int p : {7, 5, 3})
+        while (m % p == 0) { pl->radix[np++] = p; m /= p; }
+    if (np > kMixedMaxPasses) return false;
+    pl->npass = np;
+    int64_t ns = 1, off = 0, threads = 32;
+    for (int p = 0; p < np; ++p) {
+        const int r = pl->radix[p];
+        pl->ns[p] = (int)ns;
+        pl->magic[p] = ns > 1 ? (uint32_t)((((uint64_t)1) << 32) / (uint64_t)ns + 1) : 0;
+        pl->twoff[p] = (int)off;
+        if (p > 0) off += ns * (r - 1);
+        const int64_t per = (int64_t)r * (16 / r);          // samples a thread holds in a pass
+        const int64_t t = (n + per - 1) / per;
+        if (t > threads) threads = t;
+        ns *= r;
+    }
+    threads = (threads + 31) / 32 * 32;
+    if (threads > (dtype == LCT_C64 ? 1024 : 512)) return false;
+    pl->threads = (int)threads;
+    const unsigned __int128 inv = (~(unsigned __int128)0) / (unsigned __int128)(2 * n);   // 2^128/(2N)
+    pl->inv_hi = (uint64_t)(inv >> 64);
+    pl->inv_lo = (uint64_t)inv;
+    return true;
+}
+
+namespace {
+// e^{-2 pi i j r / (Ns R)} for every pass p >= 1 (j < Ns, 1 <= r < R), the
+// angle reduced exactly in integers, sine and cosine in long double.
+template <class T>
+std::vector<T> build_mixed_twiddles(const lct_mixed_plan& pl) {
+    size_t total = 0;
+    for (int p = 1; p < pl.npass; ++p) total += (size_t)pl.ns[p] * (pl.radix[p] - 1);
+    const size_t head = kMixedPlanBytes / sizeof(T);        // the plan, then the table
+    std::vector<T> out(head + 2 * (total ? total : 1), (T)0);
+    std::memcpy(out.data(), &pl, sizeof(pl));
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int p = 1; p < pl.npass; ++p) {
+        const int64_t ns = pl.ns[p], R = pl.radix[p], L = ns * R;
+        for (int64_t r = 1; r < R; ++r)
+            for (int64_t j = 0; j < ns; ++j) {
+                const int64_t q = (j * r) % L;
+                const long double ang = -two_pi * (long double)q / (long double)L;
+                const size_t e = (size_t)pl.twoff[p] + (size_t)((r - 1) * ns + j);
+                out[head + 2 * e] = (T)cosl(ang);
+                out[head + 2 * e + 1] = (T)sinl(ang);
+            }
+    }
+    return out;
+}
+}  // namespace
+
+const void* lct_mixed_twiddles(int dtype, int64_t n) {
+    lct_mixed_plan pl;
+    if (!lct_mixed_make_plan(n, dtype, &pl)) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(g_tw_mu);
+    const auto key = std::make_tuple(dev, 200 + dtype, (int)n);
+    if (dtype == LCT_C64) return cached_table(key, [&] { return build_mixed_twiddles<float>(pl); });
+    return cached_table(key, [&] { return build_mixed_twiddles<double>(pl); });
 }
 
 int lct_make_desc_host(int64_t N, const double* p, int64_t offset, lct_desc* D) {

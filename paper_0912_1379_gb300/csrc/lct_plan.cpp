@@ -363,13 +363,11 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
             return LCT_OK;
         case LCT_PREC_PLAIN64:
             // the unfused paths take powers of two only
-            if (plan->desc[0].kind == LCT_KIND_BLUE || plan->desc[0].kind == LCT_KIND_DIAGN)
-                return LCT_ERR_UNSUPPORTED;
+            if (blue_kind(plan->desc[0].kind)) return LCT_ERR_UNSUPPORTED;
             plan->prec = precision;
             return LCT_OK;
         case LCT_PREC_PLAIN32:
-            if (plan->desc[0].kind == LCT_KIND_BLUE || plan->desc[0].kind == LCT_KIND_DIAGN)
-                return LCT_ERR_UNSUPPORTED;
+            if (blue_kind(plan->desc[0].kind)) return LCT_ERR_UNSUPPORTED;
             // FP32 chirps around cuFFT C2C: complex64 plans of one N
             if (plan->dtype != LCT_C64 || plan->ragged || plan->N0 == 0) return LCT_ERR_UNSUPPORTED;
             plan->prec = precision;
@@ -500,8 +498,10 @@ lct_status lct_partition(int64_t count, const int64_t* N, const double* abcd_rei
         if (N[s] < 2 || N[s] > 65536) return LCT_ERR_N;
         const bool diag = abcd_reim && abcd_reim[8 * s + 2] == 0.0 && abcd_reim[8 * s + 3] == 0.0;
         const int l = ilog2_exact(N[s]);
-        // a DFT of N (power of two), or two DFTs of M >= 2N - 1 (other N)
+        // a DFT of N (power of two or 7-smooth, mixed radix), or two DFTs of
+        // M >= 2N - 1 (other N)
         const double dft = l >= 0 ? (double)N[s] * l
+                         : lct_mixed_ok(N[s]) ? (double)N[s] * std::ceil(std::log2((double)N[s]))
                                   : 2.0 * (double)((int64_t)1 << lct_blue_log2m(N[s])) * lct_blue_log2m(N[s]);
         cost[(size_t)s] = diag ? (double)N[s] : dft;
     }

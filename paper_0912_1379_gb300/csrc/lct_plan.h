@@ -104,8 +104,10 @@ typedef std::complex<double> cplx;
 // ---- lct_phase.cpp --------------------------------------------------------
 // log2 N for N a power of two in [2, 65536], else -1.
 int ilog2_exact(int64_t N);
-// Is this a plan of N that is not a power of two (chirp-convolution kernel)?
-inline bool blue_kind(int kind) { return kind == LCT_KIND_BLUE || kind == LCT_KIND_DIAGN; }
+// Is this a plan of N that is not a power of two (mixed-radix or chirp-convolution kernel)?
+inline bool blue_kind(int kind) {
+    return kind == LCT_KIND_BLUE || kind == LCT_KIND_DIAGN || kind == LCT_KIND_MIXED;
+}
 // round(v 2^64) mod 2^64 for a turn fraction v (|v| < 1).
 uint64_t double_to_turns64(double v);
 // Validates p = {a, b, c, d} (re, im pairs; ad - bc = 1) and fills the

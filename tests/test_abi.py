@@ -267,9 +267,12 @@ def test_phase_constants_exact(N, abcd):
                                     (4095, (0.3, -1.9, (0.3 * 0.4 - 1) / -1.9, 0.4)),
                                     (3, (1.0, 2.0, 0.5, 2.0))])
 def test_phase_constants_non_power_of_two(N, abcd):
-    """For N that is not a power of two the chirps absorb the -1/(8N) turns
-    of the convolution split: phi_in - 1/(8N), phi_out - 1/(8N), and the
-    constant is arg(dx / sqrt(2 pi i b)) alone (mpmath, 60 digits)."""
+    """N that is not a power of two (mpmath, 60 digits).  7-smooth N (1000,
+    3: the mixed-radix DFT) keeps the direct form: phi_in = a pi/(32 b N),
+    phi_out = b d/(2 pi N), and the constant -(N-1)^2/(4N) + arg(dx/sqrt(2 pi
+    i b)) turns.  Other N (4095 = 3^2 5 7 13: the chirp convolution) absorb
+    the -1/(8N) turns of the convolution split in both chirps, and the
+    constant is arg(dx/sqrt(2 pi i b)) alone."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 60
     a, b, c, d = abcd
@@ -278,14 +281,21 @@ def test_phase_constants_non_power_of_two(N, abcd):
         in_hi, in_lo, out_hi, out_lo, out_c = lct.lct_plan_phase_turns(p)
     finally:
         lct.lct_plan_destroy(p)
+    m = N
+    for q in (2, 3, 5, 7):
+        while m % q == 0:
+            m //= q
+    smooth = m == 1
     A, B, D = mpmath.mpf(a), mpmath.mpf(b), mpmath.mpf(d)
-    t_in = A * mpmath.pi / (32 * B * N) - mpmath.mpf(1) / (8 * N)
-    t_out = B * D / (2 * mpmath.pi * N) - mpmath.mpf(1) / (8 * N)
+    shift = 0 if smooth else mpmath.mpf(1) / (8 * N)
+    t_in = A * mpmath.pi / (32 * B * N) - shift
+    t_out = B * D / (2 * mpmath.pi * N) - shift
     assert abs(_turns_err((in_hi << 64) | in_lo, t_in, 128)) < 2 ** 28
     assert abs(_turns_err((out_hi << 64) | out_lo, t_out, 128)) < 2 ** 28
     dx = mpmath.pi / mpmath.sqrt(2 * N)
     pre = dx / mpmath.sqrt(2j * mpmath.pi * B)
-    assert abs(_turns_err(out_c, mpmath.arg(pre) / (2 * mpmath.pi), 64)) < 2 ** 14
+    centre = -mpmath.mpf((N - 1) ** 2 % (4 * N)) / (4 * N) if smooth else 0
+    assert abs(_turns_err(out_c, centre + mpmath.arg(pre) / (2 * mpmath.pi), 64)) < 2 ** 14
 
 
 @pytest.mark.parametrize("N", [3, 100, 4095, 65535])
@@ -320,9 +330,12 @@ def test_non_power_of_two_precision_choices():
 
 
 def test_partition_costs_non_power_of_two():
-    """A non-power-of-two N costs two DFTs of M >= 2N - 1 (here M = 2048)."""
-    owner, load = lct.lct_partition([1000, 1024], 2)
+    """A 7-smooth N costs one mixed-radix DFT (N ceil(log2 N)); another N two
+    DFTs of M >= 2N - 1 (1001 = 7 11 13: M = 2048)."""
+    owner, load = lct.lct_partition([1001, 1024], 2)
     assert sorted(load.tolist()) == [1024 * 10, 2 * 2048 * 11]
+    owner, load = lct.lct_partition([1000, 3000], 2)
+    assert sorted(load.tolist()) == [1000 * 10, 3000 * 12]
 
 
 @pytest.mark.parametrize("N,z,dtype,status", [

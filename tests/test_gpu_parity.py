@@ -248,8 +248,9 @@ def test_plain64_complex64_io():
 
 
 # --------------------------------------------------------------------------
-# N that is not a power of two: chirp - FFT_M - spectrum - inverse FFT_M -
-# chirp (M >= 2N - 1) in one kernel
+# N that is not a power of two: 7-smooth N by the mixed-radix kernel (chirp,
+# DFT_N, chirp); other N by chirp - FFT_M - spectrum - inverse FFT_M - chirp
+# (M >= 2N - 1) in one kernel (here 4095 = 3^2 5 7 13 and 8191, prime)
 # --------------------------------------------------------------------------
 NON_POW2 = [3, 5, 6, 7, 12, 100, 1000, 4095]
 
@@ -655,3 +656,38 @@ def test_ragged_full_size_workload(variant):
         lhs = np.sum(np.abs(G[o:o + N].astype(np.complex128)) ** 2) * 4 * b / np.pi
         rhs = np.sum(np.abs(buf[o:o + N].astype(np.complex128)) ** 2)
         assert abs(lhs / rhs - 1) < 2e-5
+
+
+# 7-smooth sizes that are not powers of two take the mixed-radix kernel (one
+# DFT of N); every radix (16, 8, 4, 2, 7, 5, 3) appears first, in the middle
+# and last, and alone.
+MIXED_SIZES = [3, 5, 6, 7, 9, 10, 12, 14, 15, 21, 24, 25, 27, 35, 48, 49, 96, 125, 243, 343, 384,
+               625, 729, 1000, 1536, 2187, 2401, 3000, 3072, 3125, 4000, 6000, 6144, 6561, 7168,
+               7776, 8000]
+
+
+@pytest.mark.parametrize("N", MIXED_SIZES)
+def test_mixed_radix_sizes(N):
+    count = 13 if N <= 1024 else 3
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=900 + N, dtype=np.complex128)
+    for dtype in [np.complex64, np.complex128]:
+        if dtype == np.complex128 and N > 4096:
+            continue
+        code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+        fd = f.astype(dtype)
+        ref = O.lct(fd.astype(np.complex128), params)
+        p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code)
+        try:
+            G = run(p.handle, fd, dtype)
+        finally:
+            p.destroy()
+        assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64), (N, dtype)
+        abcd = (0.37, -1.3, (0.37 * 0.8 - 1) / -1.3, 0.8)
+        p = lct.Plan.create(N, *abcd, dtype=code)
+        try:
+            G = run(p.handle, fd, dtype)
+        finally:
+            p.destroy()
+        ref = O.lct(fd.astype(np.complex128), abcd)
+        assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64), (N, dtype)
