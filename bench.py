@@ -63,7 +63,9 @@ DTYPES = {"native": "f32", "split_bf16": "bf16 hi+lo operands, f32 accumulate",
 VARIANT_KERNELS = {0: "k_xft_fused<12, float>", 1: "k_xft_fused_tma<12, false>",
                    2: "k_xft_fused_tma<12, true>", 3: "k_xft_pair<12, 2>", 4: "k_xft_pair_tma<12>",
                    5: "k_xft_cluster", 6: "k_xft_pair<12, 2, 3>",
-                   7: "k_xft_pass_a + k_xft_pass_b (two passes)", 8: "k_xft_fused_tmat<12>"}
+                   7: "k_xft_pass_a + k_xft_pass_b (two passes)", 8: "k_xft_fused_tmat<12>",
+                   10: "k_xft_fused<12, float, packed, radix 8>",
+                   11: "k_xft_fused<12, float, one signal per CTA>"}
 SPLIT_KERNELS = {"split_bf16": "k_xft_split<12, bf16, 3 products>",
                  "split_fp16": "k_xft_split<12, fp16, 3 products>",
                  "fp16": "k_xft_split<12, fp16, 1 product>"}
@@ -89,7 +91,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 path")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-clocks", action="store_true", help="skip clock sampling (profiler runs)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8", "9"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "0", "1", "2", "3", "4", "5", "6", "7", "8", "9", "10", "11"],
                     help="fused kernel variant (auto: the library's autotuner)")
     ap.add_argument("--nonpow2-n", type=int, default=3000,
                     help="nonpow2 workload: N (7-smooth: mixed radix; else chirp convolution)")

@@ -165,12 +165,20 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  *     persistent launch that takes work items from one device queue,
  *     largest N first -- the two-pass tiles of every N >= 8192, then groups
  *     of signals of N <= 4096, then the b = 0 chunks -- instead of the CUDA
- *     graph of one kernel per N (other ragged plans keep the graph).
- * LCT_ERR_ARG for an unknown variant.  Host-only. */
+ *     graph of one kernel per N (other ragged plans keep the graph);
+ * 10  schedule of variant 0 with radix-8 passes: eight samples per thread,
+ *     N/8 threads per signal (N = 16 .. 8192), packed signals per CTA;
+ * 11  schedule of variant 0 with one signal per CTA at any batch size
+ *     (N = 32 .. 16384 complex64, .. 8192 complex128; complex128 up to
+ *     N = 2048 with four samples per thread, radix-4 passes).
+ * Variants 10 and 11 are the radix and signals-per-CTA choices the
+ * autotuner times beside the others; a variant a plan cannot take falls
+ * back to variant 0.  LCT_ERR_ARG for an unknown variant.  Host-only. */
 lct_status lct_plan_set_variant(lct_plan plan, int variant);
-/* The variant set on the plan, else the default for its N (7 for N >= 32768,
- * else 0; a tuned variant in the process cache overrides the default at
- * execution). */
+/* The variant set on the plan, else the default for its N and dtype (7 for
+ * N >= 32768; for complex64 10 at N = 32 .. 256 and 11 at N = 512 .. 2048,
+ * the schedules that measured fastest there on GB300; else 0; a tuned
+ * variant in the process cache overrides the default at execution). */
 lct_status lct_plan_get_variant(lct_plan plan, int* variant);
 
 /* Autotuner: run every variant that can execute this plan on the given

@@ -288,7 +288,69 @@ cudaError_t launch_dispatch(int log2n, const void* in, void* out, const lct_desc
     }
 }
 
+// Explicit schedules for the autotuner: radix-8 passes (LE = 3, twice the
+// threads of the radix-16 schedule, packed signals per CTA), or one signal
+// per CTA with radix-16 passes (LE = 4) or, FP64, radix-4 passes (LE = 2).
+template <class R>
+cudaError_t sched_dispatch(int log2n, int le, bool one, const void* in, void* out,
+                           const lct_desc* desc, int desc_step, int64_t count, const void* tw,
+                           const int32_t* idx, int32_t* status, cudaStream_t stream) {
+    if (le == 3 && !one) {
+        switch (log2n) {
+#define LCT_CASE(L) \
+    case L: return launch_shape<L, R, false, 3>(in, out, desc, desc_step, count, tw, idx, status, stream);
+            LCT_CASE(4) LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10)
+            LCT_CASE(11) LCT_CASE(12) LCT_CASE(13)
+#undef LCT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (le == 2 && one) {
+        switch (log2n) {
+#define LCT_CASE(L) \
+    case L: return launch_shape<L, R, true, 2>(in, out, desc, desc_step, count, tw, idx, status, stream);
+            LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11)
+#undef LCT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (le == 4 && one) {
+        switch (log2n) {
+#define LCT_CASE(L) \
+    case L: return launch_shape<L, R, true, 4>(in, out, desc, desc_step, count, tw, idx, status, stream);
+            LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11)
+            LCT_CASE(12) LCT_CASE(13)
+#undef LCT_CASE
+            case 14:
+                if constexpr (sizeof(R) == 4)
+                    return launch_shape<14, R, true, 4>(in, out, desc, desc_step, count, tw, idx,
+                                                        status, stream);
+                return cudaErrorInvalidValue;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+bool lct_fused_sched_supported(int dtype, int log2n, int le, int one) {
+    if (le == 3 && !one) return log2n >= 4 && log2n <= 13;
+    if (le == 2 && one) return dtype == 1 && log2n >= 5 && log2n <= 11;
+    if (le == 4 && one) return log2n >= 5 && log2n <= (dtype == 0 ? 14 : 13);
+    return false;
+}
+
+cudaError_t lct_launch_fused_sched(int dtype, int log2n, int le, int one, const void* in, void* out,
+                                   const lct_desc* desc, int desc_step, int64_t count, const void* tw,
+                                   const int32_t* idx, int32_t* status, cudaStream_t stream) {
+    if (!lct_fused_sched_supported(dtype, log2n, le, one)) return cudaErrorInvalidValue;
+    if (dtype == 0)
+        return sched_dispatch<float>(log2n, le, one != 0, in, out, desc, desc_step, count, tw, idx,
+                                     status, stream);
+    return sched_dispatch<double>(log2n, le, one != 0, in, out, desc, desc_step, count, tw, idx,
+                                  status, stream);
+}
 
 bool lct_fused_tma_supported(int dtype, int log2n) {
     return dtype == 0 && log2n >= 8 && log2n <= 13;

@@ -103,9 +103,52 @@ bool tmat_ok(lct_plan p, const void* in, int64_t batch) {
            ((batch << log2n) % 256) == 0;
 }
 
-// Variant used when neither the plan nor the tune cache chooses one.
+// Variant used when neither the plan nor the tune cache chooses one: two
+// passes from N = 32768, else the fused kernel's schedule that measured
+// fastest on GB300 for complex64 batches (64 Mi points, per-signal
+// parameters; the schedule sweep is in the design notes).
 int default_variant(lct_dtype dtype, int log2n) {
-    return (lct_twopass_supported(dtype, log2n) && log2n >= kTwoPassDefaultLog2) ? 7 : 0;
+    if (lct_twopass_supported(dtype, log2n) && log2n >= kTwoPassDefaultLog2) return 7;
+    if (dtype == LCT_C64) {
+        if (log2n >= 5 && log2n <= 8) return 10;       // N = 32..256: radix-8 passes
+        if (log2n >= 9 && log2n <= 11) return 11;      // N = 512..2048: one signal per CTA
+    }
+    return 0;
+}
+
+// Does schedule variant 10 (radix-8 passes) or 11 (one signal per CTA)
+// apply to this N and dtype?
+bool sched_applies(lct_dtype dtype, int log2n, int variant) {
+    if (variant == 10) return lct_fused_sched_supported(dtype, log2n, 3, 0);
+    if (variant == 11)
+        return lct_fused_sched_supported(dtype, log2n, 2, 1) || lct_fused_sched_supported(dtype, log2n, 4, 1);
+    return false;
+}
+
+// Twiddle table of a schedule variant (radix-4 passes for complex128 one
+// signal per CTA up to N = 2048), or nullptr when the variant does not apply
+// to this N and dtype (or the table cannot be made).
+const void* sched_table(lct_dtype dtype, int log2n, int variant) {
+    if (variant == 10 && lct_fused_sched_supported(dtype, log2n, 3, 0))
+        return lct_twiddle_table_le(dtype, log2n, 3);
+    if (variant == 11 && lct_fused_sched_supported(dtype, log2n, 2, 1))
+        return lct_twiddle_table_le(dtype, log2n, 2);
+    if (variant == 11 && lct_fused_sched_supported(dtype, log2n, 4, 1))
+        return lct_twiddle_table(dtype, log2n);
+    return nullptr;
+}
+
+// Launch a schedule variant (10 or 11) of the fused kernel; false if it does
+// not apply (the caller then takes variant 0).
+bool launch_sched(lct_plan p, int log2n, int variant, const void* in, void* out, int desc_step,
+                  int64_t count, const int32_t* idx, cudaStream_t stream, lct_status* st) {
+    const void* tw = sched_table(p->dtype, log2n, variant);
+    if (!tw) return false;
+    const bool r4 = variant == 11 && lct_fused_sched_supported(p->dtype, log2n, 2, 1);
+    const int le = variant == 10 ? 3 : (r4 ? 2 : 4);
+    *st = from_cuda(lct_launch_fused_sched(p->dtype, log2n, le, variant == 11 ? 1 : 0, in, out, p->d_desc,
+                                           desc_step, count, tw, idx, p->d_status, stream));
+    return true;
 }
 
 int effective_variant(lct_plan p) {
@@ -190,6 +233,10 @@ lct_status run_fused(lct_plan p, const void* in, void* out, int64_t batch, int d
         return from_cuda(lct_launch_fused_pair(p->dtype, log2n, in, out, p->d_desc, desc_step,
                                                batch, tw2, stream));
     }
+    if (variant == 10 || variant == 11) {
+        lct_status st = LCT_OK;
+        if (launch_sched(p, log2n, variant, in, out, desc_step, batch, nullptr, stream, &st)) return st;
+    }
     if (variant == 8 && tmat_ok(p, in, batch))
         return from_cuda(lct_launch_fused_tmat(log2n, in, out, p->d_desc, desc_step, batch, tw,
                                                p->d_status, stream));
@@ -250,6 +297,11 @@ lct_status launch_group(lct_plan p, const lct_plan_s::group& g, const void* in, 
                                             lct_twiddle_table(p->dtype, lm), idx, p->d_status,
                                             stream));
     if (!single) return LCT_ERR_UNSUPPORTED;
+    const int gv = group_variant(p->dtype, g.log2n);
+    if (gv == 10 || gv == 11) {
+        lct_status st = LCT_OK;
+        if (launch_sched(p, g.log2n, gv, in, out, 1, g.count, idx, stream, &st)) return st;
+    }
     return from_cuda(lct_launch_fused(p->dtype, g.log2n, in, out, p->d_desc, 1, g.count,
                                       lct_twiddle_table(p->dtype, g.log2n), idx, p->d_status,
                                       stream));
@@ -297,6 +349,8 @@ lct_status build_graph(lct_plan p, const void* in, void* out) {
         if (g.log2n >= 5 && lct_fused_supported(p->dtype, g.log2n) &&
             !lct_twiddle_table(p->dtype, g.log2n))
             return LCT_ERR_OOM;
+        const int gv = group_variant(p->dtype, g.log2n);       // schedule tables before capture
+        if (sched_applies(p->dtype, g.log2n, gv) && !sched_table(p->dtype, g.log2n, gv)) return LCT_ERR_OOM;
     }
     if (!p->cap) {
         if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -547,8 +601,11 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
         return LCT_OK;
     }
     const int saved = plan->variant;
-    int candidates[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int candidates[16] = {0};
     int n_cand = 1;
+    // schedules of the fused kernel: radix-8 passes, one signal per CTA
+    if (sched_applies(plan->dtype, plan->desc[0].log2n, 10)) candidates[n_cand++] = 10;
+    if (sched_applies(plan->dtype, plan->desc[0].log2n, 11)) candidates[n_cand++] = 11;
     if (lct_fused_pair8_supported(plan->dtype, plan->desc[0].log2n)) candidates[n_cand++] = 6;
     if (lct_cluster_local_log2(plan->dtype, plan->desc[0].log2n) >= 0 &&
         lct_fused_supported(plan->dtype, plan->desc[0].log2n))

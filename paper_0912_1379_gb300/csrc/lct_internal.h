@@ -301,6 +301,15 @@ cudaError_t lct_launch_mehler_spectrum(int dtype, int64_t n, double a_h, uint64_
                                        uint64_t phi_lo, double c_re, double c_im,
                                        const lct_desc& D, lct_desc* d_desc, void* spec,
                                        int32_t* status, const void* tw, cudaStream_t stream);
+// Fused kernel with an explicit schedule (autotuner variants 10 and 11):
+// le = 3 (radix-8 passes, N/8 threads per signal, packed signals per CTA),
+// or one signal per CTA with le = 4 (radix-16 passes) or, complex128 up to
+// N = 2048, le = 2 (radix-4 passes).  tw: lct_twiddle_table_le(dtype,
+// log2n, le).
+bool lct_fused_sched_supported(int dtype, int log2n, int le, int one);
+cudaError_t lct_launch_fused_sched(int dtype, int log2n, int le, int one, const void* in, void* out,
+                                   const lct_desc* desc, int desc_step, int64_t count, const void* tw,
+                                   const int32_t* idx, int32_t* status, cudaStream_t stream);
 // Mixed-radix plan of one N (kind LCT_KIND_MIXED): the passes' radices
 // (16, 8, 4, 2, 7, 5, 3), Ns_p (product of the earlier radices), the exact
 // divisor magic floor(2^32 / Ns_p) + 1 (b / Ns_p = umulhi(b, magic) for

@@ -391,7 +391,7 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision) {
 }
 
 lct_status lct_plan_set_variant(lct_plan plan, int variant) {
-    if (!plan || variant < 0 || variant > 9) return LCT_ERR_ARG;
+    if (!plan || variant < 0 || variant > 11) return LCT_ERR_ARG;
     plan->variant = variant;
     return LCT_OK;
 }

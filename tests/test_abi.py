@@ -114,24 +114,33 @@ def test_execute_validation_without_gpu():
 def test_variant_selection_host_only():
     p = lct.lct_plan_create(1024, 1.0, 2.0, 0.5, 2.0)
     try:
-        assert lct.lct_plan_get_variant(p) == 0
+        assert lct.lct_plan_get_variant(p) == 11          # measured default schedule at N = 1024
         lct.lct_plan_set_variant(p, 1)
         assert lct.lct_plan_get_variant(p) == 1
         lct.lct_plan_set_variant(p, 7)
         assert lct.lct_plan_get_variant(p) == 7
         lct.lct_plan_set_variant(p, 8)
         assert lct.lct_plan_get_variant(p) == 8
-        for bad in (10, -1):
+        lct.lct_plan_set_variant(p, 11)
+        assert lct.lct_plan_get_variant(p) == 11
+        for bad in (12, -1):
             with pytest.raises(lct.LctError) as e:
                 lct.lct_plan_set_variant(p, bad)
             assert e.value.status == 1
     finally:
         lct.lct_plan_destroy(p)
     # default: two passes from N = 32768 up, else variant 0
-    for N, want in [(4096, 0), (16384, 0), (32768, 7), (65536, 7)]:
+    for N, want in [(16, 0), (32, 10), (256, 10), (512, 11), (2048, 11), (4096, 0), (16384, 0),
+                    (32768, 7), (65536, 7)]:
         p = lct.lct_plan_create(N, 1.0, 2.0, 0.5, 2.0)
         try:
             assert lct.lct_plan_get_variant(p) == want
+        finally:
+            lct.lct_plan_destroy(p)
+        # complex128 keeps variant 0 below the two-pass sizes
+        p = lct.lct_plan_create(N, 1.0, 2.0, 0.5, 2.0, dtype=lct.LCT_C128)
+        try:
+            assert lct.lct_plan_get_variant(p) == (7 if N >= 32768 else 0)
         finally:
             lct.lct_plan_destroy(p)
 

@@ -105,7 +105,7 @@ def test_uniform_batch_per_signal_params(N, count, seed):
 
 
 @pytest.mark.parametrize("N,count", [(256, 100), (1024, 333), (4096, 700), (8192, 30), (16384, 9)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11])
 def test_kernel_variants(N, count, variant):
     """Both fused variants (one CTA per group / persistent with bulk-async
     prefetch) on per-signal parameters, with a ragged last group."""
@@ -213,7 +213,7 @@ def test_autotune_picks_a_valid_variant():
         xin = to_dev(f, np.complex64)
         out = torch.empty_like(xin)
         v = p.autotune(xin, out, count)
-        assert v in (0, 1, 2, 3, 4, 5, 6, 8)
+        assert v in (0, 1, 2, 3, 4, 5, 6, 8, 10, 11)
         G = run(p.handle, f, np.complex64)
     finally:
         p.destroy()
@@ -691,3 +691,60 @@ def test_mixed_radix_sizes(N):
             p.destroy()
         ref = O.lct(fd.astype(np.complex128), abcd)
         assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64), (N, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("N", [16, 32, 64, 512, 2048, 8192])
+def test_schedule_variants_both_dtypes(N, dtype):
+    """The autotuner's schedules (10: radix-8 passes; 11: one signal per CTA)
+    in both dtypes, shared parameters, a partly empty last CTA."""
+    count = 37 if N <= 2048 else 5
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, count, seed=N + 11, dtype=np.complex128)
+    abcd = (0.9, -0.7, (0.9 * 1.2 - 1) / -0.7, 1.2)
+    code = lct.LCT_C64 if dtype == np.complex64 else lct.LCT_C128
+    ref = O.lct(f.astype(dtype).astype(np.complex128), abcd)
+    for variant in (10, 11):
+        p = lct.Plan.create(N, *abcd, dtype=code).set_variant(variant)
+        try:
+            G = run(p.handle, f.astype(dtype), dtype)
+        finally:
+            p.destroy()
+        assert rel_l2(G, ref).max() < (TOL32 if dtype == np.complex64 else TOL64), (N, variant)
+
+
+def test_ragged_groups_take_schedule_defaults():
+    """Ragged groups of N = 256, 512, 1024 and 2048 run their default
+    schedules (variants 10, 11, 11, 11) inside the graph, through the signal
+    index lists."""
+    specs = [256, 1024, 2048, 256, 1024, 2048, 512]
+    rng = np.random.default_rng(5)
+    Ns, abcds, offs, sigs = [], [], [], []
+    off = 0
+    for N in specs:
+        b = rng.uniform(0.5, 2.0) * rng.choice([-1, 1])
+        a, d = rng.uniform(-1.5, 1.5), rng.uniform(-1.5, 1.5)
+        abcd = np.array([a, b, (a * d - 1) / b, d], dtype=np.complex128)
+        x = O.nodes(N)
+        f = np.exp(-x * x / 8) * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+        Ns.append(N)
+        abcds.append(abcd)
+        offs.append(off)
+        sigs.append(f)
+        off += N + 3
+    buf = np.zeros(off, dtype=np.complex128)
+    for o, f in zip(offs, sigs):
+        buf[o:o + len(f)] = f
+    p = lct.Plan.batch(Ns, np.array(abcds), offs, dtype=lct.LCT_C64)
+    try:
+        xin = torch.from_numpy(buf.astype(np.complex64)).cuda()
+        out = torch.zeros_like(xin)
+        lct.lct_execute(p.handle, xin, out, len(Ns))
+        torch.cuda.synchronize()
+        assert lct.lct_device_status(p.handle) == 0
+        ob = out.cpu().numpy()
+    finally:
+        p.destroy()
+    for o, f, abcd in zip(offs, sigs, abcds):
+        ref = O.lct(f.astype(np.complex64).astype(np.complex128), abcd)
+        assert rel_l2(ob[o:o + len(f)], ref).max() < TOL32
