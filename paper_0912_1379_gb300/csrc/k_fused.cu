@@ -71,7 +71,10 @@ k_xft_fused(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out,
         if (active) f = ld_stream(in + base + n);
         v[e] = cmul(f, pre_w<L, R>(D, n, decay));
     }
-    dft_signal<L, -1, false, LE>(v, buf, i, tw);
+    // signals of at most 32 consecutive threads synchronise their warp only
+    // (CTAs of whole warps; a CTA smaller than a warp keeps the CTA barrier)
+    if constexpr (S::T <= 32 && F::THREADS % 32 == 0) dft_signal_warp<L, -1, false, LE>(v, buf, i, tw);
+    else dft_signal<L, -1, false, LE>(v, buf, i, tw);
     // global store (sample i + e T) with the post-chirp and scale
     if (active) {
         const R sc = (R)D.scale;

@@ -137,22 +137,30 @@ __device__ __forceinline__ void smem_load(cpx<R>* v, const cpx<R>* buf, int i) {
     for (int e = 0; e < S::E; ++e) v[e] = buf[pad_idx<PS>(i + e * S::T)];
 }
 
+// Exchange barrier: the whole CTA, or only the warp when every signal's
+// threads lie within one warp (WS: T <= 32 consecutive threads per signal).
+template <bool WS>
+__device__ __forceinline__ void exchange_sync() {
+    if constexpr (WS) __syncwarp();
+    else __syncthreads();
+}
+
 // Passes p..P-1, the first of which reads the shared-memory output of pass p-1.
-template <int L, int p, int SGN, bool TWC, class R, int LE, int PS,
+template <int L, int p, int SGN, bool TWC, class R, int LE, int PS, bool WS = false,
           bool DONE = (p >= shape<L, LE>::P)>
 struct passes_from {
     __device__ __forceinline__ static void run(cpx<R>* v, cpx<R>* buf, int i,
                                                const cpx<R>* __restrict__ tw) {
-        if (p > 1) __syncthreads();          // previous exchange fully read
+        if (p > 1) exchange_sync<WS>();      // previous exchange fully read
         smem_store<L, p - 1, LE, PS>(v, buf, i);
-        __syncthreads();
+        exchange_sync<WS>();
         smem_load<L, LE, PS>(v, buf, i);
         butterflies<L, p, SGN, TWC, LE>(v, i, tw);
-        passes_from<L, p + 1, SGN, TWC, R, LE, PS>::run(v, buf, i, tw);
+        passes_from<L, p + 1, SGN, TWC, R, LE, PS, WS>::run(v, buf, i, tw);
     }
 };
-template <int L, int p, int SGN, bool TWC, class R, int LE, int PS>
-struct passes_from<L, p, SGN, TWC, R, LE, PS, true> {
+template <int L, int p, int SGN, bool TWC, class R, int LE, int PS, bool WS>
+struct passes_from<L, p, SGN, TWC, R, LE, PS, WS, true> {
     __device__ __forceinline__ static void run(cpx<R>*, cpx<R>*, int, const cpx<R>* __restrict__) {}
 };
 
@@ -163,6 +171,17 @@ __device__ __forceinline__ void dft_signal(cpx<R>* v, cpx<R>* buf, int i,
                                            const cpx<R>* __restrict__ tw) {
     butterflies<L, 0, SGN, TWC, LE>(v, i, tw);
     passes_from<L, 1, SGN, TWC, R, LE, PS>::run(v, buf, i, tw);
+}
+
+// The same for a signal whose T <= 32 threads are consecutive (lie within one
+// warp): the exchanges synchronise that warp only, so the other signals of
+// the CTA are not held at its barriers.
+template <int L, int SGN, bool TWC = false, int LE = 4, int PS = 4, class R>
+__device__ __forceinline__ void dft_signal_warp(cpx<R>* v, cpx<R>* buf, int i,
+                                                const cpx<R>* __restrict__ tw) {
+    static_assert(shape<L, LE>::T <= 32, "signal wider than a warp");
+    butterflies<L, 0, SGN, TWC, LE>(v, i, tw);
+    passes_from<L, 1, SGN, TWC, R, LE, PS, true>::run(v, buf, i, tw);
 }
 
 // Streaming global load that does not allocate in L1 (keeps the twiddle
