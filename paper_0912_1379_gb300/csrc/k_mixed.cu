@@ -114,6 +114,14 @@ struct mx_k {
 // banks within each half-warp.
 __device__ __forceinline__ int mx_pad(int e) { return e + (e >> 4); }
 
+// Exchange barrier: a signal of 32 threads is one warp (slices start at
+// multiples of T), which then synchronises alone; wider signals use the CTA
+// barrier.  T is the same for every thread of the launch.
+__device__ __forceinline__ void mx_sync(int T) {
+    if (T == 32) __syncwarp();
+    else __syncthreads();
+}
+
 // Exact turn of the chirp and centring at sample k (m = 2k - n + 1).
 template <class R>
 __device__ __forceinline__ cpx<R> mx_chirp(uint64_t phi_hi, uint64_t phi_lo, uint64_t inv_hi,
@@ -190,7 +198,7 @@ __device__ __forceinline__ void mx_pass(const lct_mixed_plan& pl, int p, cpx<R>*
 #pragma unroll
     for (int k = 0; k < K; ++k) dft_fwd<RAD>(v[k]);
     if (!last) {
-        if (!first) __syncthreads();                 // every input read before any output
+        if (!first) mx_sync(T);                      // every input read before any output
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int b = i + k * T;
@@ -202,7 +210,7 @@ __device__ __forceinline__ void mx_pass(const lct_mixed_plan& pl, int p, cpx<R>*
                 for (int s = 0; s < RAD; ++s) buf[mx_pad(o + s * ns)] = v[k][s];
             }
         }
-        __syncthreads();
+        mx_sync(T);
     } else if (active) {
         // last pass: ns * RAD = n, so b < ns and the output index is b + s ns
         const uint64_t out_hi = Dp->out_hi, out_lo = Dp->out_lo, out_c = Dp->out_c;

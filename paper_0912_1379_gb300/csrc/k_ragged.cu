@@ -53,7 +53,8 @@ __device__ __forceinline__ void fused_item(const cpx<float>* __restrict__ in, cp
             if (active) f = ld_stream(in + D.offset + n);
             v[e] = cmul(f, pre_w<L, float>(D, n, decay));
         }
-        dft_signal<L, -1>(v, buf, i, tw);
+        if constexpr (S::T <= 32) dft_signal_warp<L, -1>(v, buf, i, tw);   // signal within a warp
+        else dft_signal<L, -1>(v, buf, i, tw);
         if (active) {
             const float sc = (float)D.scale;
 #pragma unroll
