@@ -169,8 +169,8 @@ lct_status lct_plan_set_precision(lct_plan plan, lct_precision precision);
  * 10  schedule of variant 0 with radix-8 passes: eight samples per thread,
  *     N/8 threads per signal (N = 16 .. 8192), packed signals per CTA;
  * 11  schedule of variant 0 with one signal per CTA at any batch size
- *     (N = 32 .. 16384 complex64, .. 8192 complex128; complex128 up to
- *     N = 2048 with four samples per thread, radix-4 passes).
+ *     (N = 32 .. 2048, where variant 0 packs several signals per CTA;
+ *     complex128 with four samples per thread, radix-4 passes).
  * Variants 10 and 11 are the radix and signals-per-CTA choices the
  * autotuner times beside the others; a variant a plan cannot take falls
  * back to variant 0.  LCT_ERR_ARG for an unknown variant.  Host-only. */
@@ -292,8 +292,14 @@ lct_status frft_hermite_status(lct_stream_t stream);
  * 3 doubles per signal for batch plans, 3 doubles summed over `batch` for
  * single plans; `in` (f) and `out` (G) of the forward call are then
  * required.  All pointers are device memory.  Supported: uniform N <= 4096,
- * b != 0; parameter gradients for real parameters only
- * (LCT_ERR_UNSUPPORTED otherwise).  The plan keeps a workspace of 3 doubles
+ * b != 0; parameter gradients for real parameters only.  The input gradient
+ * alone (grad_abd NULL) is also computed for every other plan of one N the
+ * forward path takes -- N = 8192 .. 65536, N that is not a power of two,
+ * b = 0 -- with real parameters and signals at s N: as conj(L' conj(g)), L'
+ * the forward transform with its two chirps exchanged (the DFT part of the
+ * factorisation is symmetric), i.e. two conjugation passes around one
+ * forward launch in grad_in (descriptors for L' kept by the plan).
+ * LCT_ERR_UNSUPPORTED otherwise.  The plan keeps a workspace of 3 doubles
  * per signal for the reductions. */
 lct_status lct_backward(lct_plan plan, const void* grad_out, const void* in, const void* out,
                         void* grad_in, double* grad_abd, int64_t batch, lct_stream_t stream);

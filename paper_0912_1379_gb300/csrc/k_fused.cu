@@ -322,13 +322,7 @@ cudaError_t sched_dispatch(int log2n, int le, bool one, const void* in, void* ou
 #define LCT_CASE(L) \
     case L: return launch_shape<L, R, true, 4>(in, out, desc, desc_step, count, tw, idx, status, stream);
             LCT_CASE(5) LCT_CASE(6) LCT_CASE(7) LCT_CASE(8) LCT_CASE(9) LCT_CASE(10) LCT_CASE(11)
-            LCT_CASE(12) LCT_CASE(13)
 #undef LCT_CASE
-            case 14:
-                if constexpr (sizeof(R) == 4)
-                    return launch_shape<14, R, true, 4>(in, out, desc, desc_step, count, tw, idx,
-                                                        status, stream);
-                return cudaErrorInvalidValue;
             default: return cudaErrorInvalidValue;
         }
     }
@@ -340,7 +334,8 @@ cudaError_t sched_dispatch(int log2n, int le, bool one, const void* in, void* ou
 bool lct_fused_sched_supported(int dtype, int log2n, int le, int one) {
     if (le == 3 && !one) return log2n >= 4 && log2n <= 13;
     if (le == 2 && one) return dtype == 1 && log2n >= 5 && log2n <= 11;
-    if (le == 4 && one) return log2n >= 5 && log2n <= (dtype == 0 ? 14 : 13);
+    // from N = 4096 the packed shape already holds one signal per CTA
+    if (le == 4 && one) return log2n >= 5 && log2n <= 11;
     return false;
 }
 

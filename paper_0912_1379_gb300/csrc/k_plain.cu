@@ -278,3 +278,28 @@ cudaError_t lct_launch_plain32_post(const void* work, void* out, const lct_desc*
         (const cpx<float>*)work, (cpx<float>*)out, desc, desc_step, count, log2n);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Elementwise complex conjugate (in == out allowed): the conjugations around
+// the forward kernels in the adjoint of plans the backward kernel does not take.
+// ---------------------------------------------------------------------------
+namespace {
+template <class R>
+__global__ void k_conj(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const cpx<R> v = in[e];
+        out[e] = {v.x, -v.y};
+    }
+}
+}  // namespace
+
+cudaError_t lct_launch_conj(int dtype, const void* in, void* out, int64_t n, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const int th = 256;
+    if (dtype == 0)
+        k_conj<float><<<grid_for(n, th), th, 0, stream>>>((const cpx<float>*)in, (cpx<float>*)out, n);
+    else
+        k_conj<double><<<grid_for(n, th), th, 0, stream>>>((const cpx<double>*)in, (cpx<double>*)out, n);
+    return cudaGetLastError();
+}

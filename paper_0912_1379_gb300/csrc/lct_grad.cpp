@@ -7,6 +7,7 @@
 #include <cmath>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 namespace lcth {
@@ -82,6 +83,34 @@ lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G,
                                               p->d_partial + 3 * p->partial_count, stream));
 }
 
+// Adjoint of a plan the backward kernel does not take (N >= 8192, N that is
+// not a power of two, b = 0), real parameters: the discrete operator is
+// L = S_out K S_in with diagonal chirps S and a symmetric K (the kernel
+// e^{-i pi m_j m_k/(2N)} of Sec. 3, or the identity for b = 0), so
+//   L^H g = conj(L' conj(g)),  L' = S_in K S_out,
+// the forward transform with the two chirps exchanged (for b = 0 the plan's
+// own diagonal).  Two conjugation passes around one forward launch, in place
+// in h; signals contiguous (offset s N).
+lct_status run_adjoint_forward(lct_plan p, const void* g, void* h, int64_t batch, cudaStream_t stream) {
+    if (!p->d_desc_adj) {
+        std::vector<lct_desc> a(p->desc);
+        for (lct_desc& D : a)
+            if (D.kind == LCT_KIND_XFT || D.kind == LCT_KIND_MIXED || D.kind == LCT_KIND_BLUE) {
+                std::swap(D.in_hi, D.out_hi);
+                std::swap(D.in_lo, D.out_lo);
+            }
+        const size_t bytes = sizeof(lct_desc) * a.size();
+        if (cudaMalloc(&p->d_desc_adj, bytes) != cudaSuccess) return LCT_ERR_OOM;
+        if (cudaMemcpy(p->d_desc_adj, a.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return LCT_ERR_CUDA;
+    }
+    const int64_t n = batch * p->N0;
+    lct_status st = from_cuda(lct_launch_conj(p->dtype, g, h, n, stream));
+    if (st == LCT_OK) st = execute_locked(p, p->d_desc_adj, h, h, batch, stream);
+    if (st == LCT_OK) st = from_cuda(lct_launch_conj(p->dtype, h, h, n, stream));
+    return st;
+}
+
 }  // namespace lcth
 
 using namespace lcth;
@@ -103,11 +132,20 @@ lct_status lct_backward(lct_plan plan, const void* grad_out, const void* in, con
         if (!real_params(plan)) return LCT_ERR_UNSUPPORTED;
     }
     if (plan->ragged || plan->N0 == 0 || plan->prec != LCT_PREC_NATIVE) return LCT_ERR_UNSUPPORTED;
+    bool gen = lct_gen_supported(plan->dtype, plan->desc[0].log2n, 0);
     for (const lct_desc& D : plan->desc)
-        if (D.kind != LCT_KIND_XFT) return LCT_ERR_UNSUPPORTED;
+        if (D.kind != LCT_KIND_XFT) gen = false;
     std::lock_guard<std::mutex> g(plan->mu);
     st = ensure_device(plan);
     if (st != LCT_OK) return st;
+    if (!gen) {
+        // input gradient only: through the forward kernels
+        if (grad_abd || !real_params(plan) || (plan->is_batch && !plan->contiguous))
+            return LCT_ERR_UNSUPPORTED;
+        st = run_adjoint_forward(plan, grad_out, grad_in, batch, (cudaStream_t)stream_);
+        if (st == LCT_OK && debug_on()) st = debug_check(plan, grad_in, batch, (cudaStream_t)stream_);
+        return st;
+    }
     st = run_backward(plan, grad_out, in, out, grad_in, grad_abd, batch, 0, 1, 1, plan->N0,
                       (cudaStream_t)stream_);
     if (st == LCT_OK && debug_on()) st = debug_check(plan, grad_in, batch, (cudaStream_t)stream_);

@@ -310,6 +310,8 @@ bool lct_fused_sched_supported(int dtype, int log2n, int le, int one);
 cudaError_t lct_launch_fused_sched(int dtype, int log2n, int le, int one, const void* in, void* out,
                                    const lct_desc* desc, int desc_step, int64_t count, const void* tw,
                                    const int32_t* idx, int32_t* status, cudaStream_t stream);
+// out[e] = conj(in[e]) for e < n (in == out allowed).
+cudaError_t lct_launch_conj(int dtype, const void* in, void* out, int64_t n, cudaStream_t stream);
 // Mixed-radix plan of one N (kind LCT_KIND_MIXED): the passes' radices
 // (16, 8, 4, 2, 7, 5, 3), Ns_p (product of the earlier radices), the exact
 // divisor magic floor(2^32 / Ns_p) + 1 (b / Ns_p = umulhi(b, magic) for

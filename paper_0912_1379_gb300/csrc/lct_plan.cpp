@@ -147,8 +147,10 @@ void release_device(lct_plan p) {
     p->rg_sync_bytes = 0;
     cudaFree(p->d_coef);
     cudaFree(p->d_partial);
+    cudaFree(p->d_desc_adj);
     p->d_coef = nullptr;
     p->d_partial = nullptr;
+    p->d_desc_adj = nullptr;
     p->partial_count = 0;
     if (cur != p->device && cur >= 0) cudaSetDevice(cur);
     p->fft_valid = false;

@@ -87,6 +87,8 @@ struct lct_plan_s {
     // backward: per-signal gradient coefficients and reduction workspace
     double* d_coef = nullptr;
     double* d_partial = nullptr;
+    // backward through the forward kernels: descriptors with the two chirps exchanged
+    lct_desc* d_desc_adj = nullptr;
     int64_t partial_count = 0;
     // offset properties, fixed at creation: every offset even (16-byte signal
     // starts when `in` is 16-byte aligned) and offset[s] == s N0

@@ -284,3 +284,113 @@ def test_2d_full_size_fields():
             fd = (4 * d2 - d1) / 3
             got = gp[3 * axis + q]
             assert abs(got - fd) < 1e-4 * max(abs(fd), 1e-3 * np.abs(gp).max()), (axis, comp, got, fd)
+
+
+# --------------------------------------------------------------------------
+# input gradient of plans the backward kernel does not take: N = 8192 ..
+# 65536, N that is not a power of two, b = 0 (through the forward kernels)
+# --------------------------------------------------------------------------
+BIG = [(8192, np.complex64, True), (16384, np.complex128, False), (32768, np.complex64, True),
+       (3000, np.complex64, True), (3000, np.complex128, False), (3001, np.complex64, False),
+       (1000, np.complex128, True)]
+
+
+def _adjoint_run(p, g, f, count):
+    xg, xf = cu(g), cu(f)
+    h = torch.empty_like(xg)
+    lct.lct_backward(p.handle, xg, None, None, h, None, count)
+    G = torch.empty_like(xf)
+    p.execute(xf, G, count)
+    torch.cuda.synchronize()
+    assert lct.lct_device_status(p.handle) == 0
+    return h.cpu().numpy(), G.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,dt,per_signal", BIG)
+def test_adjoint_through_forward_kernels(N, dt, per_signal):
+    count = 3 if N <= 8192 else 2
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=N + 5, dtype=dt)
+    rng = np.random.default_rng(N + 6)
+    g = (rng.standard_normal((count, N)) + 1j * rng.standard_normal((count, N))).astype(dt)
+    code = lct.LCT_C64 if dt == np.complex64 else lct.LCT_C128
+    abcd = params if per_signal else params[0]
+    p = (lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code) if per_signal
+         else lct.Plan.create(N, *abcd, dtype=code))
+    try:
+        h, G = _adjoint_run(p, g, f, count)
+    finally:
+        p.destroy()
+    tol = 1e-12 if dt == np.complex128 else 1e-5
+    ref = O.lct_adjoint(g.astype(np.complex128), abcd)
+    assert rel_l2(h, ref).max() < tol, (N, dt)
+    lhs = np.vdot(g.astype(np.complex128).ravel(), G.astype(np.complex128).ravel())
+    rhs = np.vdot(h.astype(np.complex128).ravel(), f.astype(np.complex128).ravel())
+    assert abs(lhs - rhs) < (1e-11 if dt == np.complex128 else 1e-4) * abs(lhs)
+
+
+@pytest.mark.parametrize("dt", [np.complex64, np.complex128])
+def test_adjoint_identity_at_65536(dt):
+    """<L f, g> = <f, L^H g> for the two-pass path (the oracle's O(N^2)
+    adjoint is checked at 32768)."""
+    N, count = 65536, 2
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=65, dtype=dt)
+    rng = np.random.default_rng(66)
+    g = (rng.standard_normal((count, N)) + 1j * rng.standard_normal((count, N))).astype(dt)
+    code = lct.LCT_C64 if dt == np.complex64 else lct.LCT_C128
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=code)
+    try:
+        h, G = _adjoint_run(p, g, f, count)
+    finally:
+        p.destroy()
+    for s in range(count):
+        lhs = np.vdot(g[s].astype(np.complex128), G[s].astype(np.complex128))
+        rhs = np.vdot(h[s].astype(np.complex128), f[s].astype(np.complex128))
+        assert abs(lhs - rhs) < (1e-11 if dt == np.complex128 else 1e-4) * abs(lhs)
+
+
+@pytest.mark.parametrize("N", [256, 300])
+def test_adjoint_b_zero(N):
+    abcd = (1 / 1.4, 0.0, 0.35, 1.4)
+    x = O.nodes(N)
+    _, f = W.uniform_batch(x, 3, seed=N, dtype=np.complex128)
+    g = np.random.default_rng(N).standard_normal((3, N)) + 0j
+    p = lct.Plan.create(N, *abcd, dtype=lct.LCT_C128)
+    try:
+        h, _ = _adjoint_run(p, g, f, 3)
+    finally:
+        p.destroy()
+    assert rel_l2(h, O.lct_adjoint(g, abcd)).max() < 1e-12
+
+
+def test_adjoint_through_forward_rejects_what_it_cannot_do():
+    N = 8192
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, 3, seed=1, dtype=np.complex64)
+    xf = cu(f)
+    out = torch.empty_like(xf)
+    gp = torch.zeros(3, dtype=torch.float64, device="cuda")
+    p = lct.Plan.create(N, *params[0], dtype=lct.LCT_C64)
+    try:
+        with pytest.raises(lct.LctError) as e:           # parameter gradients: N <= 4096 only
+            lct.lct_backward(p.handle, xf, xf, out, out, gp, 3)
+        assert e.value.status == 10
+    finally:
+        p.destroy()
+    z = 0.6 + 0.3j                                       # complex parameters
+    abcd = O.abcd_of_z(z)
+    p = lct.Plan.create(N, *[complex(v) for v in abcd], dtype=lct.LCT_C64)
+    try:
+        with pytest.raises(lct.LctError) as e:
+            lct.lct_backward(p.handle, xf, None, None, out, None, 3)
+        assert e.value.status == 10
+    finally:
+        p.destroy()
+    gapped = lct.Plan.batch([N] * 2, params[:2], [0, N + 4], dtype=lct.LCT_C64)
+    try:
+        with pytest.raises(lct.LctError) as e:           # signals not at s N
+            lct.lct_backward(gapped.handle, xf, None, None, out, None, 2)
+        assert e.value.status == 10
+    finally:
+        gapped.destroy()
