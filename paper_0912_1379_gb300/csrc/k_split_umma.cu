@@ -188,17 +188,27 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
             }
             // Stockham exchange into pass p + 1: output j of group g goes to
             // position pos = (g - k) 16 + k + j NS_p (k = g mod NS_p), i.e.
-            // group pos mod 256, element pos / 256, twiddled by
-            // e^{-2 pi i e' k' / (16 NS_{p+1})} (table entry), k' = group mod NS_{p+1}
+            // group pos mod 256, element e' = pos / 256 = g / 16 (the same for
+            // all j), twiddled by e^{-2 pi i e' k' / (16 NS_{p+1})} with
+            // k' = group mod NS_{p+1} = j (p = 0) or k + 16 j (p = 1): the
+            // powers w0 w1^j of w1 = e^{-2 pi i e'/256}, w0 = 1 or
+            // e^{-2 pi i e' k/4096}, formed in registers (one or two sincospi
+            // and a running product) instead of table loads.
             const int g = p == 0 ? t : transpose16(t);
-            const int ns = p == 0 ? 1 : 16, ns1 = p == 0 ? 16 : 256, tw_off = p == 0 ? 0 : 240;
+            const int ns = p == 0 ? 1 : 16;
             const int k = g & (ns - 1);
+            const int e1 = g >> 4;
+            const cpx<float> w1 = twiddle_exact<float, -1>(e1, 256);
+            cpx<float> u = p == 0 ? cpx<float>{1.f, 0.f} : twiddle_exact<float, -1>(e1 * k, 4096);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int pos = (g - k) * 16 + k + j * ns;
-                const int g1 = pos & 255, e1 = pos >> 8;
+                const int g1 = pos & 255;
                 cpx<float> y = {v[2 * j], v[2 * j + 1]};
-                if (e1 > 0) y = cmul(y, ld_tw<float>(tw + tw_off + (e1 - 1) * ns1 + (g1 & (ns1 - 1))));
+                if (e1 > 0) {
+                    y = cmul(y, u);
+                    u = cmul(u, w1);
+                }
                 uint32_t hi, lo;
                 split_c(y, hi, lo);
                 const int row = p == 0 ? transpose16(g1) : g1;
