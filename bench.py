@@ -74,8 +74,10 @@ SPLIT_KERNELS = {"split_bf16": "k_xft_split<12, bf16, 3 products>",
 def kernel_name(variant, precision):
     if variant is not None:
         return VARIANT_KERNELS[variant]
-    if precision == "split_bf16" and os.environ.get("LCT_SPLIT_KERNEL", "") != "mma":
-        return "k_xft_split_umma (tcgen05, bf16, 3 products)"     # the library's default
+    if os.environ.get("LCT_SPLIT_KERNEL", "") != "mma":          # the library's default
+        return {"split_bf16": "k_xft_split_umma (tcgen05, bf16, 3 products)",
+                "split_fp16": "k_xft_split_umma (tcgen05, fp16, 3 products)",
+                "fp16": "k_xft_split_umma (tcgen05, fp16, 1 product)"}[precision]
     return SPLIT_KERNELS[precision]
 
 
@@ -379,6 +381,22 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
         if s in pos:
             k = pos[s]
             buf[offs[k]:offs[k] + Ns[s]] = sig
+    # autotuned schedule: each N of the batch is tuned once on a uniform batch of
+    # its own signal count (synthetic G1 signals); the ragged graph's groups then
+    # take the tuned kernel variant / schedule from the library's cache
+    schedules = {}
+    if args.variant == "auto":
+        for n in sorted({int(v) for v in Ns[mine]}):
+            cnt = int((Ns[mine] == n).sum())
+            tp, tf = W.uniform_batch(lct.lct_input_grid(n), cnt, seed=W.SEED_RAGGED + n,
+                                     dtype=np.complex64)
+            tplan = lct.Plan.batch([n] * cnt, tp, np.arange(cnt, dtype=np.int64) * n,
+                                   dtype=lct.LCT_C64)
+            t_in = torch.from_numpy(tf).cuda()
+            t_out = torch.empty_like(t_in)
+            schedules[n] = tplan.autotune(t_in, t_out, cnt, torch.cuda.current_stream())
+            tplan.destroy()
+            del t_in, t_out
     plan = lct.Plan.batch(Ns[mine], abcd[mine], offs, dtype=lct.LCT_C64)
     persistent = args.variant == "9"
     if persistent:
@@ -452,6 +470,7 @@ def ragged_arm(args, rank, world, lct, torch, barrier, max_over_ranks, local):
                                                     (W.KIND_FOURIER, "Fourier"), (W.KIND_B0, "b=0"))),
                                       W.SEED_RAGGED),
                        "points": total, "signals_by_N": by_n,
+                       "autotuned_variant_by_N": schedules or None,
                        "sharding": "lct_partition over %d ranks (cost N log2 N, largest first); "
                                    "load imbalance %.2e" % (world, load.max() / load.mean() - 1),
                        "l2": "inputs larger than L2 (%.2f GB per buffer at one GPU), no flush" % (total * 8 / 1e9),
