@@ -28,9 +28,17 @@
 // transpose(t) in pass 1.
 //
 // Operand layout (umma_desc.h): K-major, no swizzle, core matrices of 8 rows
-// x 8 BF16 (16 bytes per row), LBO = 128 bytes along K, SBO = 512 bytes per 8
-// rows (32 K values per row).
+// x 8 16-bit values (16 bytes per row), LBO = 128 bytes along K, SBO = 512
+// bytes per 8 rows (32 K values per row).
+//
+// The same kernel takes FP16 operands (kind::f16, both A and B FP16): split
+// hi + lo with three products, or hi alone with one product (TERMS = 1).
+// FP16 signals are scaled by a power of two after the pre-chirp so that
+// their largest component is below 1 (each radix-16 pass grows it at most
+// 16-fold: below 4096 after the three, inside the FP16 range), and the
+// output by the inverse.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "xft_engine.cuh"
 #include "xft_chirp.cuh"
@@ -48,25 +56,66 @@ constexpr uint32_t kSmem = 2 * kPlane + 2 * kBPlane;       // 36 KB
 constexpr uint32_t kSLbo = 128, kSSbo = 512, kTmemCols = 64;
 constexpr uint64_t kSWaitNs = 2000000000ull;
 
-// Byte offset of element (row, k) of a 32-wide K-major BF16 operand.
+// Byte offset of element (row, k) of a 32-wide K-major 16-bit operand.
 __host__ __device__ constexpr uint32_t boff(uint32_t r, uint32_t k) {
     return (r >> 3) * kSSbo + (k >> 3) * kSLbo + (r & 7) * 16 + (k & 7) * 2;
 }
 __device__ __forceinline__ int transpose16(int g) { return ((g & 15) << 4) | (g >> 4); }
 
-__device__ __forceinline__ uint32_t bf2(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
+// A pair of 16-bit operand values (a low, b high) in BF16 or FP16, and back.
+template <int FMT>
+__device__ __forceinline__ uint32_t pk2(float a, float b) {
+    if constexpr (FMT == umma::kFmtBF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
 }
-__device__ __forceinline__ float2 unbf2(uint32_t v) {
-    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
-    return __bfloat1622float2(h);
+template <int FMT>
+__device__ __forceinline__ float2 upk2(uint32_t v) {
+    if constexpr (FMT == umma::kFmtBF16) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h = *reinterpret_cast<__half2*>(&v);
+        return __half22float2(h);
+    }
 }
-// hi = rn(re, im), lo = rn((re, im) - hi), each a BF16 pair (re low, im high)
+// hi = rn(re, im), lo = rn((re, im) - hi) (TERMS = 3), each a pair (re low, im high)
+template <int FMT, int TERMS>
 __device__ __forceinline__ void split_c(cpx<float> v, uint32_t& hi, uint32_t& lo) {
-    hi = bf2(v.x, v.y);
-    const float2 h = unbf2(hi);
-    lo = bf2(v.x - h.x, v.y - h.y);
+    hi = pk2<FMT>(v.x, v.y);
+    if constexpr (TERMS == 3) {
+        const float2 h = upk2<FMT>(hi);
+        lo = pk2<FMT>(v.x - h.x, v.y - h.y);
+    } else {
+        lo = 0;
+    }
+}
+// One 16-bit value at p (B operand set-up), and its rounded value.
+template <int FMT>
+__device__ __forceinline__ float st16(unsigned char* p, float v) {
+    if constexpr (FMT == umma::kFmtBF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(p) = h;
+        return __bfloat162float(h);
+    } else {
+        const __half h = __float2half_rn(v);
+        *reinterpret_cast<__half*>(p) = h;
+        return __half2float(h);
+    }
+}
+// 2^-ex (DOWN) or 2^ex for m the bit pattern of max |component| = f 2^ex,
+// f in [0.5, 1) (1 for a zero signal); ex clamped to [-125, 125] so that both
+// factors are normal numbers.
+template <bool DOWN>
+__device__ __forceinline__ float exp2_of_max(uint32_t m) {
+    int ex = 0;
+    if (m) frexpf(__uint_as_float(m), &ex);
+    ex = min(max(ex, -125), 125);
+    return ldexpf(1.f, DOWN ? -ex : ex);
 }
 
 __constant__ float kCosT16[16] = {
@@ -79,6 +128,7 @@ __device__ __forceinline__ bool bar_wait_all(uint64_t* bar, uint32_t parity) {
     return xasync::mbar_wait(bar, parity, kSWaitNs);
 }
 
+template <int FMT, int TERMS>
 __global__ void __launch_bounds__(kST, 4)
 k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
                  const lct_desc* __restrict__ desc, int desc_step, int64_t count,
@@ -86,6 +136,7 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_slot;
+    __shared__ uint32_t s_amax[kST / 32];                   // FP16: per-warp max |component|
     const int t = threadIdx.x, warp = t >> 5;
     if (warp == 0) umma::tmem_alloc(&tmem_slot, kTmemCols);
     if (t == 0) {
@@ -100,10 +151,8 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
         const int m = (j * e) & 15;
         const float re = kCosT16[m], im = -kCosT16[(m + 12) & 15];      // F_je = re + i im
         const float v = cp == 0 ? (c == 0 ? re : -im) : (c == 0 ? im : re);
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-        *reinterpret_cast<__nv_bfloat16*>(sm + kOffBhi + boff(n, k)) = h;
-        *reinterpret_cast<__nv_bfloat16*>(sm + kOffBlo + boff(n, k)) = l;
+        const float h = st16<FMT>(sm + kOffBhi + boff(n, k), v);
+        if (TERMS == 3) st16<FMT>(sm + kOffBlo + boff(n, k), v - h);
     }
     umma::fence_before_sync();
     __syncthreads();
@@ -111,7 +160,7 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
     const uint32_t tmem = tmem_slot;
     // this thread's accumulator row: tile warp >> 2 (columns 32 tile ..), lane t
     const uint32_t my_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
-    constexpr uint32_t idesc = umma::instr_desc(umma::kFmtBF16, umma::kFmtBF16, 128, 32);
+    constexpr uint32_t idesc = umma::instr_desc(FMT, FMT, 128, 32);       // A and B of one type
     const uint32_t a_base = xasync::smem_addr(sm);
     uint32_t phase = 0;
     bool ok = true;
@@ -121,20 +170,39 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
         const int64_t base = desc_step ? D.offset : sig * (int64_t)kSN;
         const bool decay = (D.flags & LCT_FLAG_DECAY) != 0;
         // pass 0 input: samples t + 256 e with the pre-chirp, into A row t
+        float inv_scale = 1.f;                              // FP16: undoes the input scale
         {
-            uint32_t hi[16], lo[16];
+            cpx<float> f[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int n = t + kST * e;
-                const cpx<float> f = ld_stream(in + base + n);
-                split_c(cmul(f, pre_w<kSL, float>(D, n, decay)), hi[e], lo[e]);
+                f[e] = cmul(ld_stream(in + base + n), pre_w<kSL, float>(D, n, decay));
             }
+            if constexpr (FMT == umma::kFmtF16) {
+                uint32_t m = 0;
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    m = max(m, __float_as_uint(fmaxf(fabsf(f[e].x), fabsf(f[e].y))));
+                m = __reduce_max_sync(0xffffffffu, m);
+                if ((t & 31) == 0) s_amax[warp] = m;
+                __syncthreads();
+#pragma unroll
+                for (int w = 0; w < kST / 32; ++w) m = max(m, s_amax[w]);
+                const float sc_in = exp2_of_max<true>(m);
+                inv_scale = exp2_of_max<false>(m);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) f[e] = cscale(f[e], sc_in);
+            }
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) split_c<FMT, TERMS>(f[e], hi[e], lo[e]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 *reinterpret_cast<uint4*>(sm + boff(t, 8 * q)) =
                     make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
-                *reinterpret_cast<uint4*>(sm + kOffAlo + boff(t, 8 * q)) =
-                    make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+                if (TERMS == 3)
+                    *reinterpret_cast<uint4*>(sm + kOffAlo + boff(t, 8 * q)) =
+                        make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
             }
         }
 #pragma unroll 1
@@ -155,8 +223,10 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
                         const uint64_t bh = umma::smem_desc(a_base + kOffBhi + ks * 2 * kSLbo, kSLbo, kSSbo);
                         const uint64_t bl = umma::smem_desc(a_base + kOffBlo + ks * 2 * kSLbo, kSLbo, kSSbo);
                         umma::mma_f16(d, ah, bh, idesc, ks > 0 ? 1u : 0u);
-                        umma::mma_f16(d, ah, bl, idesc, 1u);
-                        umma::mma_f16(d, al, bh, idesc, 1u);
+                        if (TERMS == 3) {
+                            umma::mma_f16(d, ah, bl, idesc, 1u);
+                            umma::mma_f16(d, al, bh, idesc, 1u);
+                        }
                     }
                 }
                 umma::commit(&bar);
@@ -177,7 +247,7 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
             umma::fence_before_sync();
             if (p == 2) {
                 // thread t holds X[t + 256 j]: post-chirp, scale, store
-                const float sc = (float)D.scale;
+                const float sc = (float)D.scale * inv_scale;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int n = t + kST * j;
@@ -210,11 +280,11 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
                     u = cmul(u, w1);
                 }
                 uint32_t hi, lo;
-                split_c(y, hi, lo);
+                split_c<FMT, TERMS>(y, hi, lo);
                 const int row = p == 0 ? transpose16(g1) : g1;
                 const uint32_t o = boff((uint32_t)row, (uint32_t)(2 * e1));
                 *reinterpret_cast<uint32_t*>(sm + o) = hi;
-                *reinterpret_cast<uint32_t*>(sm + kOffAlo + o) = lo;
+                if (TERMS == 3) *reinterpret_cast<uint32_t*>(sm + kOffAlo + o) = lo;
             }
         }
     }
@@ -229,24 +299,24 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
 
 bool lct_split_umma_supported(int dtype, int log2n) { return dtype == 0 && log2n == kSL; }
 
-cudaError_t lct_launch_split_umma(int log2n, const void* in, void* out, const lct_desc* desc,
-                                  int desc_step, int64_t count, const void* tw, int32_t* status,
-                                  cudaStream_t stream) {
-    if (log2n != kSL || !tw) return cudaErrorInvalidValue;
+namespace {
+template <int FMT, int TERMS>
+cudaError_t launch_umma(const void* in, void* out, const lct_desc* desc, int desc_step, int64_t count,
+                        const void* tw, int32_t* status, cudaStream_t stream) {
+    auto kern = k_xft_split_umma<FMT, TERMS>;
     static int blocks_per_sm[64] = {}, sms[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!blocks_per_sm[dev]) {
-        e = cudaFuncSetAttribute(k_xft_split_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmem);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
         if (e != cudaSuccess) return e;
         // resident CTAs per SM from the kernel's own registers and shared
         // memory (and 8 by tensor memory: 64 of 512 columns each); more CTAs
         // than fit only wait for a slot, as the CTAs never wait on each other
         cudaFuncAttributes fa;
-        if ((e = cudaFuncGetAttributes(&fa, k_xft_split_umma)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
         int regs_sm = 0, smem_sm = 0;
         if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
@@ -261,7 +331,20 @@ cudaError_t lct_launch_split_umma(int log2n, const void* in, void* out, const lc
     if (count <= 0) return cudaSuccess;
     int64_t grid = (int64_t)blocks_per_sm[dev] * sms[dev];
     if (grid > count) grid = count;
-    k_xft_split_umma<<<(unsigned)grid, kST, kSmem, stream>>>(
-        (const cpx<float>*)in, (cpx<float>*)out, desc, desc_step, count, (const cpx<float>*)tw, status);
+    kern<<<(unsigned)grid, kST, kSmem, stream>>>((const cpx<float>*)in, (cpx<float>*)out, desc, desc_step,
+                                                count, (const cpx<float>*)tw, status);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t lct_launch_split_umma(int prec, int log2n, const void* in, void* out, const lct_desc* desc,
+                                  int desc_step, int64_t count, const void* tw, int32_t* status,
+                                  cudaStream_t stream) {
+    if (log2n != kSL || !tw) return cudaErrorInvalidValue;
+    switch (prec) {
+        case 1: return launch_umma<umma::kFmtBF16, 3>(in, out, desc, desc_step, count, tw, status, stream);
+        case 2: return launch_umma<umma::kFmtF16, 3>(in, out, desc, desc_step, count, tw, status, stream);
+        case 3: return launch_umma<umma::kFmtF16, 1>(in, out, desc, desc_step, count, tw, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }

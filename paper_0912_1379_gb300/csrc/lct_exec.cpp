@@ -65,8 +65,8 @@ lct_status run_plain(lct_plan p, const void* in, void* out, int64_t count, int d
 }
 }  // namespace
 
-// Split BF16 at N = 4096 runs on tcgen05 unless LCT_SPLIT_KERNEL=mma selects
-// the mma.sync kernel (a diagnostic, read once).
+// The split modes at N = 4096 run on tcgen05 unless LCT_SPLIT_KERNEL=mma
+// selects the mma.sync kernel (a diagnostic, read once).
 bool split_on_tcgen05() {
     static const bool on = [] {
         const char* e = std::getenv("LCT_SPLIT_KERNEL");
@@ -519,10 +519,9 @@ lct_status execute_locked(lct_plan plan, const lct_desc* desc, const void* in, v
         plan->prec == LCT_PREC_FP16) {
         const void* tw = lct_twiddle_table(plan->dtype, log2n);
         if (log2n >= 5 && !tw) return LCT_ERR_OOM;
-        if (plan->prec == LCT_PREC_SPLIT_BF16 && lct_split_umma_supported(plan->dtype, log2n) &&
-            split_on_tcgen05())
-            return from_cuda(lct_launch_split_umma(log2n, in, out, plan->d_desc, desc_step, batch, tw,
-                                                   plan->d_status, stream));
+        if (lct_split_umma_supported(plan->dtype, log2n) && split_on_tcgen05())
+            return from_cuda(lct_launch_split_umma((int)plan->prec, log2n, in, out, plan->d_desc,
+                                                   desc_step, batch, tw, plan->d_status, stream));
         return from_cuda(lct_launch_split((int)plan->prec, log2n, in, out, plan->d_desc,
                                           desc_step, batch, tw, tma_aligned(plan, in) ? 1 : 0,
                                           plan->contiguous ? 1 : 0, plan->d_status, stream));

@@ -209,11 +209,12 @@ cudaError_t lct_launch_selftest_wait(int which, uint64_t limit_ns, int32_t* word
 // bulk-async copies (a timed-out wait records LCT_DEV_TIMEOUT in *status);
 // contiguous: signal s of the launch starts at element s N of `in` (one
 // copy per tile).
-// The split-BF16 mode on the 5th-generation tensor cores (tcgen05.mma,
+// The three modes on the 5th-generation tensor cores (tcgen05.mma,
 // accumulators in tensor memory), N = 4096: persistent CTAs, one signal at a
-// time; a timed-out wait records LCT_DEV_TIMEOUT.  tw: lct_twiddle_table(0, 12).
+// time; a timed-out wait records LCT_DEV_TIMEOUT.  prec: the mode numbers
+// above.  tw: lct_twiddle_table(0, 12).
 bool lct_split_umma_supported(int dtype, int log2n);
-cudaError_t lct_launch_split_umma(int log2n, const void* in, void* out, const lct_desc* desc,
+cudaError_t lct_launch_split_umma(int prec, int log2n, const void* in, void* out, const lct_desc* desc,
                                   int desc_step, int64_t count, const void* tw, int32_t* status,
                                   cudaStream_t stream);
 cudaError_t lct_launch_split(int mode, int log2n, const void* in, void* out, const lct_desc* desc,

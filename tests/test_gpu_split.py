@@ -204,3 +204,28 @@ def test_tcgen05_split_bf16_n4096_complex_z_and_gapped_offsets():
     ref = O.lct(f.astype(np.complex128), params)
     for s in range(count):
         assert rel_l2(Gb[offs[s]:offs[s] + N], ref[s]) < 1e-5
+
+
+@pytest.mark.parametrize("mode", ["split_fp16", "fp16"])
+def test_tcgen05_fp16_scaling_at_n4096(mode):
+    """The FP16 modes at N = 4096 run on tcgen05 with a per-signal
+    power-of-two scale: signals from 1e-30 to 1e30 and a zero signal, each
+    one CTA's work, stay inside the FP16 range."""
+    prec, tol = MODES[mode]
+    N = 4096
+    scales = np.array([1e-30, 1e30, 1.0, 0.0, 1e-20, 3e20, 1e-3, 7.0, 1e10, 1e-10, 2.0])
+    count = len(scales)
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=41, dtype=np.complex128)
+    f = f * scales[:, None]
+    p = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=lct.LCT_C64)
+    p.set_precision(prec)
+    try:
+        G = run(p.handle, f.astype(np.complex64))
+    finally:
+        p.destroy()
+    assert np.all(G[3] == 0)
+    keep = scales != 0
+    assert np.all(np.isfinite(G[keep]))
+    ref = O.lct(f[keep].astype(np.complex64).astype(np.complex128), params[keep])
+    assert rel_l2(G[keep], ref).max() < tol
