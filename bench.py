@@ -1191,8 +1191,9 @@ def main():
         nbytes = count * N * 8
         e2e = {"value": world * n_points / (ems * 1e-3), "unit": "points/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ems,
-               "api": "lct_execute_host on pinned host buffers (32 MiB chunks: copy-in, transform, "
-                      "copy-out pipelined on three streams)"}
+               "api": "lct_execute_host on pinned host buffers (mapped page-locked memory: the "
+                      "kernels read the input and write the output over the host link in place; "
+                      "the bytes above cross it every step)"}
 
     cpu = None
     accuracy = None

@@ -200,11 +200,15 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                        lct_stream_t stream);
 
 /* lct_execute on host buffers: h_in/h_out are host memory (page-locked for
- * overlap; pageable memory works but each copy then blocks the host).  The
- * batch is split into chunks of about 32 MiB that are copied in, transformed
- * and copied out on three plan-owned streams with two plan-owned device
- * staging pairs, so the copies in both directions overlap each other and the
- * kernels.  Ordered after the work already queued on `stream`; `stream`
+ * overlap; pageable memory works but each copy then blocks the host).  When
+ * both are page-locked and mapped into the device's address space (memory
+ * from cudaHostAlloc / cudaMallocHost, e.g. pinned torch tensors) and the
+ * plan runs the native path with a plain-load kernel variant (not 1, 2, 4,
+ * 8), the kernels read and write them directly over the host link, with no
+ * staging.  Otherwise the batch is split into chunks of about 32 MiB that
+ * are copied in, transformed and copied out on three plan-owned streams with
+ * two plan-owned device staging pairs, so the copies in both directions
+ * overlap each other and the kernels.  Ordered after the work already queued on `stream`; `stream`
  * waits for the last copy-out (the call itself returns after queueing).
  * Calls on one plan must be ordered (one stream).  Plans from
  * lct_plan_create[_complex] or batch plans of one N with offset[s] = s N;

@@ -676,6 +676,19 @@ lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
     return st;
 }
 
+// Is p page-locked host memory mapped into the device's address space?
+// Then *dp is its device address.
+static bool host_mapped(const void* p, void** dp) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();                  // not a CUDA pointer: clear the query's error
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dp = a.devicePointer;
+    return true;
+}
+
 lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
                             lct_stream_t stream_) {
     trace_range trace("lct_execute_host");
@@ -688,6 +701,19 @@ lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_
     std::lock_guard<std::mutex> g(plan->mu);
     lct_status st = ensure_device(plan);
     if (st != LCT_OK) return st;
+    // Page-locked buffers the device can address: the kernels read and write
+    // them in place over the host link, with no staging copies (measured on
+    // GB300: 3.28 against 3.46 ms per GiB in each direction).  Kept to the
+    // kernels that load with plain instructions: not the bulk-copy and
+    // tensor-map variants (1, 2, 4, 8) nor the split precisions.
+    {
+        void* din = nullptr;
+        void* dout = nullptr;
+        const int v = effective_variant(plan);
+        if (plan->prec == LCT_PREC_NATIVE && v != 1 && v != 2 && v != 4 && v != 8 &&
+            host_mapped(h_in, &din) && host_mapped(h_out, &dout))
+            return execute_locked(plan, plan->d_desc, din, dout, batch, stream);
+    }
     const int64_t chunk = host_chunk(plan) < batch ? host_chunk(plan) : batch;
     if ((st = ensure_host_state(plan, chunk)) != LCT_OK) return st;
     const int64_t N = plan->N0;

@@ -79,3 +79,21 @@ def test_host_pageable_memory_and_fp64():
     finally:
         plan.destroy()
     assert np.array_equal(got, ref_dev)
+
+
+def test_host_staged_path_for_bulk_copy_variants():
+    """Page-locked buffers are read in place by the plain-load kernels; a
+    bulk-copy variant (1) keeps the chunked staging path: both bit-identical
+    to the device run."""
+    N, count = 4096, 5000
+    x = O.nodes(N)
+    params, f = W.uniform_batch(x, count, seed=77, dtype=np.complex64)
+    for variant in (0, 1):
+        plan = lct.Plan.batch([N] * count, params, np.arange(count) * N, dtype=lct.LCT_C64)
+        plan.set_variant(variant)
+        try:
+            ref_dev = device_result(plan, f)
+            got = host_result(plan, f)
+        finally:
+            plan.destroy()
+        assert np.array_equal(got, ref_dev), variant
