@@ -25,12 +25,13 @@ struct blue_shape {
     static constexpr int THREADS = T * SPC;
 };
 
-// Resident threads per SM the register budget is sized for: 512 (128
-// registers a thread below 1024-thread CTAs) -- the two DFTs of this kernel
-// need more than the single-DFT kernel's 64.
+// Resident threads per SM the register budget is sized for: 1024 (64
+// registers a thread).  The two DFTs then spill a few hundred bytes to L1,
+// but twice the warps hide more latency: measured 10-11% faster at M = 8192
+// than 512 threads at 128 registers without spills.
 template <int L, class R>
 constexpr int blue_min_blocks() {
-    constexpr int per_sm = 512;
+    constexpr int per_sm = 1024;
     constexpr int b = per_sm / blue_shape<L>::THREADS;
     return b > 0 ? b : 1;
 }
