@@ -52,6 +52,10 @@ TRAFFIC_FILES = {
     "k_xft_split<12, bf16, 3 products>": ("traffic_xft_split_bf16_n4096.json", SPLIT_SOURCES),
     "k_xft_split_umma (tcgen05, bf16, 3 products)": ("traffic_xft_split_umma_bf16_n4096.json",
                                                      SPLIT_UMMA_SOURCES),
+    "k_xft_split_umma (tcgen05, fp16, 3 products)": ("traffic_xft_split_umma_fp16_n4096.json",
+                                                     SPLIT_UMMA_SOURCES),
+    "k_xft_split_umma (tcgen05, fp16, 1 product)": ("traffic_xft_split_umma_fp16x1_n4096.json",
+                                                    SPLIT_UMMA_SOURCES),
     "k_xft_split<12, fp16, 3 products>": ("traffic_xft_split_fp16_n4096.json", SPLIT_SOURCES),
     "k_xft_split<12, fp16, 1 product>": ("traffic_xft_split_fp16x1_n4096.json", SPLIT_SOURCES),
 }
