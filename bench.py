@@ -145,10 +145,9 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(n_points: int, kernel: str):
-    """DRAM bytes per launch of `kernel` from its committed ncu summary, if
-    it was taken on the current kernel source (else None), scaled to this
-    launch size."""
+def kernel_profile(kernel: str):
+    """The committed ncu summary of `kernel` if it was taken on the current
+    kernel source, else None."""
     if kernel not in TRAFFIC_FILES:
         return None
     fname, sources = TRAFFIC_FILES[kernel]
@@ -158,6 +157,15 @@ def traffic_per_launch(n_points: int, kernel: str):
     except Exception:
         return None
     if j.get("kernel_hash") != kernel_hash(sources) or j.get("kernel") != kernel:
+        return None
+    return j
+
+
+def traffic_per_launch(n_points: int, kernel: str):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary,
+    scaled to this launch size (None without a current summary)."""
+    j = kernel_profile(kernel)
+    if j is None:
         return None
     per_point = float(j["dram_bytes"]) / float(j["points"])
     return per_point * n_points
@@ -1137,6 +1145,11 @@ def main():
                 "kernel": kernel_name(variant, args.precision) + " (N=4096, complex64)",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": n_points * BYTES_PER_POINT}
+    if args.precision != "native":
+        # tensor-pipe activity of the same kernel source (ncu, one launch)
+        prof = kernel_profile(kernel_name(variant, args.precision))
+        if prof is not None and "tensor_pipe_active_pct" in prof:
+            roofline["tensor_pipe_active_pct"] = prof["tensor_pipe_active_pct"]
 
     # the unfused paths on the same batch: FP64 (the named comparison) and FP32
     plain = plain32 = None

@@ -263,26 +263,25 @@ k_xft_split_umma(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out
             // k' = group mod NS_{p+1} = j (p = 0) or k + 16 j (p = 1): the
             // powers w0 w1^j of w1 = e^{-2 pi i e'/256}, w0 = 1 or
             // e^{-2 pi i e' k/4096}, formed in registers (one or two sincospi
-            // and a running product) instead of table loads.
+            // and a running product) instead of table loads.  The A row of
+            // output j is 16 j + g mod 16 in both exchanges (transpose16 of
+            // group g1 = 16 (g mod 16) + j for p = 0; g1 = g mod 16 + 16 j for
+            // p = 1), so a thread's 16 stores step by 16 rows = 2 SBO bytes
+            // from the offset of j = 0.
             const int g = p == 0 ? t : transpose16(t);
-            const int ns = p == 0 ? 1 : 16;
-            const int k = g & (ns - 1);
+            const int k = p == 0 ? 0 : (g & 15);
             const int e1 = g >> 4;
             const cpx<float> w1 = twiddle_exact<float, -1>(e1, 256);
             cpx<float> u = p == 0 ? cpx<float>{1.f, 0.f} : twiddle_exact<float, -1>(e1 * k, 4096);
+            const uint32_t o0 = boff((uint32_t)(g & 15), (uint32_t)(2 * e1));
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int pos = (g - k) * 16 + k + j * ns;
-                const int g1 = pos & 255;
                 cpx<float> y = {v[2 * j], v[2 * j + 1]};
-                if (e1 > 0) {
-                    y = cmul(y, u);
-                    u = cmul(u, w1);
-                }
+                y = cmul(y, u);                             // u = 1 exactly when e' = 0
+                u = cmul(u, w1);
                 uint32_t hi, lo;
                 split_c<FMT, TERMS>(y, hi, lo);
-                const int row = p == 0 ? transpose16(g1) : g1;
-                const uint32_t o = boff((uint32_t)row, (uint32_t)(2 * e1));
+                const uint32_t o = o0 + (uint32_t)j * (2 * kSSbo);
                 *reinterpret_cast<uint32_t*>(sm + o) = hi;
                 if (TERMS == 3) *reinterpret_cast<uint32_t*>(sm + kOffAlo + o) = lo;
             }
