@@ -38,6 +38,14 @@
  *
  * Streams are CUDA runtime streams (cudaStream_t); NULL is the legacy
  * default stream.
+ *
+ * Threads.  Entry points may be called from several host threads.  Calls
+ * on one plan are serialised by the plan; the entry points that launch
+ * kernels also hold one process-wide lock while they enqueue work (the
+ * launchers cache per-device launch configurations on first use), so
+ * concurrent calls on different plans are safe, and their kernels overlap
+ * when they are given different streams.  lct_execute_host and
+ * lct_plan_autotune wait for the device while they hold that lock.
  */
 #ifndef LCT_H
 #define LCT_H

@@ -594,6 +594,7 @@ extern "C" {
 lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t batch,
                              lct_stream_t stream_) {
     trace_range trace("lct_plan_autotune");
+    launch_lock launch;
     if (!plan) return LCT_ERR_ARG;
     if (plan->prec != LCT_PREC_NATIVE || plan->N0 == 0 || plan->desc[0].kind != LCT_KIND_XFT) {
         plan->variant = 0;
@@ -660,6 +661,7 @@ lct_status lct_plan_autotune(lct_plan plan, const void* in, void* out, int64_t b
 lct_status lct_execute(lct_plan plan, const void* in, void* out, int64_t batch,
                        lct_stream_t stream_) {
     trace_range trace("lct_execute");
+    launch_lock launch;
     if (!plan) return LCT_ERR_ARG;
     if (batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
@@ -692,6 +694,7 @@ static bool host_mapped(const void* p, void** dp) {
 lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_t batch,
                             lct_stream_t stream_) {
     trace_range trace("lct_execute_host");
+    launch_lock launch;
     if (!plan || !h_in || !h_out || batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
@@ -767,6 +770,7 @@ lct_status lct_execute_host(lct_plan plan, const void* h_in, void* h_out, int64_
 lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                         int64_t batch, lct_dtype dtype, lct_stream_t stream) {
     trace_range trace("frft_execute");
+    launch_lock launch;
     cplx z(z_re, z_im);
     double az = std::abs(z);
     if (!std::isfinite(az) || az == 0.0 || az > 1.0 + 1e-15) return LCT_ERR_ARG;
@@ -821,6 +825,7 @@ lct_status frft_execute(int64_t N, double z_re, double z_im, const void* in, voi
 lct_status frft_mehler_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                                int64_t batch, lct_dtype dtype, lct_stream_t stream_) {
     trace_range trace("frft_mehler_execute");
+    launch_lock launch;
     if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
     if (N < 2 || N > (dtype == LCT_C64 ? kBlueMaxN64 : kBlueMaxN128)) return LCT_ERR_N;
     lct_desc D;

@@ -120,6 +120,7 @@ extern "C" {
 lct_status lct_backward(lct_plan plan, const void* grad_out, const void* in, const void* out,
                         void* grad_in, double* grad_abd, int64_t batch, lct_stream_t stream_) {
     trace_range trace("lct_backward");
+    launch_lock launch;
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (plan->is_batch && batch != plan->count) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
@@ -191,6 +192,7 @@ lct_status lct2d_plan_create(lct2d_plan* out, int64_t ny, int64_t nx, const doub
 lct_status lct2d_execute(lct2d_plan plan, const void* in, void* mid, void* out, int64_t batch,
                          lct_stream_t stream_) {
     trace_range trace("lct2d_execute");
+    launch_lock launch;
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
     lct_status st = check_ptr(mid, plan->dtype);
@@ -217,6 +219,7 @@ lct_status lct2d_backward(lct2d_plan plan, const void* grad_out, const void* in,
                           const void* out, void* grad_mid, void* grad_in, double* grad_abd,
                           int64_t batch, lct_stream_t stream_) {
     trace_range trace("lct2d_backward");
+    launch_lock launch;
     if (!plan || batch < 0) return LCT_ERR_ARG;
     if (batch == 0) return LCT_OK;
     const void* ptrs[4] = {grad_out, grad_mid, grad_in, grad_abd ? mid : grad_out};
@@ -265,6 +268,7 @@ extern "C" lct_status lct_transpose(lct_dtype dtype, const void* in, void* out, 
     lct_status st = check_ptr(in, dtype);
     if (st == LCT_OK) st = check_ptr(out, dtype);
     if (st != LCT_OK) return st;
+    launch_lock launch;
     return from_cuda(lct_launch_transpose((int)dtype, in, out, rows, cols, vec, batch,
                                           (cudaStream_t)stream));
 }

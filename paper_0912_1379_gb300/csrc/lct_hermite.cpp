@@ -147,6 +147,7 @@ extern "C" {
 lct_status frft_hermite_execute(int64_t N, double z_re, double z_im, const void* in, void* out,
                                 int64_t batch, lct_dtype dtype, lct_stream_t stream_) {
     lcth::trace_range trace("frft_hermite_execute");
+    lcth::launch_lock launch;
     if (N < 2 || N > kHermMaxN) return LCT_ERR_N;
     if (dtype != LCT_C64 && dtype != LCT_C128) return LCT_ERR_DTYPE;
     const double az = std::hypot(z_re, z_im);
@@ -194,6 +195,7 @@ lct_status frft_hermite_status(lct_stream_t stream) {
 lct_status frft_hermite_basis(int64_t N, double* x, double* U) {
     if (N < 2 || N > kHermMaxN) return LCT_ERR_N;
     if (!x) return LCT_ERR_ARG;
+    lcth::launch_lock launch;
     herm_basis b;
     lct_status st = herm_get(N, &b);
     if (st != LCT_OK) return st;

@@ -208,12 +208,18 @@ lct_status ensure_device(lct_plan p) {
     return LCT_OK;
 }
 
+std::recursive_mutex& launch_mutex() {
+    static std::recursive_mutex m;
+    return m;
+}
+
 // Debug mode (LCT_DEBUG=1 in the environment, or lct_set_debug): every
 // lct_execute / lct_backward synchronises its stream, scans the outputs for
 // non-finite samples and reports the device status word.
 namespace {
 std::atomic<int> g_debug{-1};
 }  // namespace
+
 bool debug_on() {
     int v = g_debug.load();
     if (v < 0) {

@@ -154,6 +154,21 @@ lct_status run_backward(lct_plan p, const void* g, const void* f, const void* G,
 
 inline size_t sample_bytes(lct_dtype dtype) { return dtype == LCT_C64 ? 8 : 16; }
 
+// Launch lock of the entry points that run kernels, taken before any plan's
+// own lock.  The kernel launchers keep per-device launch configurations
+// (resident CTAs per multiprocessor, shared-memory opt-ins) in plain statics
+// filled by their first launch on a device; one process-wide lock around
+// the host-side submission makes those first writes happen before every
+// later read, from any thread.  Recursive: an entry point may call another
+// (frft_execute runs lct_execute, lct2d_execute runs lct_execute).  It is
+// held only while launches are enqueued (and the waits of lct_execute_host
+// and lct_plan_autotune), not while kernels run.
+std::recursive_mutex& launch_mutex();
+struct launch_lock {
+    launch_lock() : g(launch_mutex()) {}
+    std::lock_guard<std::recursive_mutex> g;
+};
+
 // NVTX range over an entry point (visible in Nsight timelines; costs a
 // call into the NVTX stub when no tool is attached).
 struct trace_range {
